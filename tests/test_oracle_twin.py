@@ -1,0 +1,40 @@
+"""The C oracle against the independent NumPy twin on tiny volumes (<= 16^3)."""
+import numpy as np
+import pytest
+
+import numpy_twin as twin
+import oracle
+from phantom import make_blob_pair, random_volume
+
+
+@pytest.mark.parametrize("dims", [(5, 7, 3), (16, 16, 16), (9, 4, 11)])
+def test_primitives_match_twin(dims):
+    vol = random_volume(dims, seed=sum(dims)) * 100
+    np.testing.assert_allclose(oracle.grad(vol), twin.grad(vol), atol=1e-12, rtol=0)
+    for sigma in (0.6, 1.0, 1.7):
+        np.testing.assert_allclose(oracle.gauss3(vol, sigma), twin.gauss3(vol, sigma),
+                                   atol=1e-11, rtol=0)
+    np.testing.assert_allclose(oracle.downsample(vol), twin.downsample(vol), atol=1e-11)
+    u = np.stack([random_volume(dims, seed=s) * 3 for s in (1, 2, 3)])
+    np.testing.assert_allclose(oracle.warp(vol, u), twin.interp(vol, *[
+        g + u[c] for c, g in enumerate(twin.grid(vol.shape))]), atol=1e-11)
+    nx, ny, nz = dims
+    fine = (2 * nx - 1, 2 * ny, 2 * nz - 1)
+    np.testing.assert_allclose(oracle.upsample(u, fine), twin.upsample(u, fine[::-1]),
+                               atol=1e-12)
+    np.testing.assert_allclose(oracle.ic_field(u * 0.2), twin.ic_field(u * 0.2), atol=1e-11)
+
+
+@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("levels", [1, 2])
+def test_registration_matches_twin(variant, levels):
+    S, M = make_blob_pair((16, 13, 11), (0.8, -0.6, 0.4), seed=variant + 1, n_blobs=10,
+                          sigma_vox=2.5, noise=1.0)
+    iters = [5] if levels == 1 else [3, 5]
+    r = oracle.register(S, M, variant=variant, levels=levels, iters=iters, alpha=0.4,
+                        threaded=False, return_raw=True)
+    u, stats = twin.register(S, M, variant, levels, iters, alpha=0.4)
+    np.testing.assert_allclose(r["raw"], u, atol=1e-12, rtol=0)
+    np.testing.assert_allclose(r["stats"], stats, rtol=1e-12, atol=1e-12)
+    if variant == 5:
+        np.testing.assert_allclose(r["u"], twin.ic_field(u), atol=1e-11)
