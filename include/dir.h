@@ -1,0 +1,187 @@
+/*
+ * dir.h -- C ABI of the GB300 demons deformable image registration library
+ * (libdir.so).
+ *
+ * The library registers a moving volume M to a static volume S with the
+ * demons algorithm and its variants as defined in Gu et al., "Implementation
+ * and evaluation of various demons deformable image registration algorithms on
+ * GPU": every iteration warps M by the current displacement field with
+ * trilinear interpolation (Sec. 2.5), computes a per-voxel demons force
+ * (Eqs. 1-6), adds the update, smooths the total field with a Gaussian
+ * (Sec. 2.1, Sec. 2.5) and reduces the mean squared difference and the field
+ * norms used by the relative-norm stop test (Sec. 2.4), inside a coarse-to-fine
+ * pyramid with factor-2 down-sampling and field up-sampling (Sec. 2.3).
+ *
+ * Conventions
+ *   Volumes are dense, x-contiguous: voxel (i, j, k) is element
+ *   i + nx * (j + ny * k) (Sec. 2.5: x as rows, y as columns, z as frames).
+ *   A displacement field is three planar float arrays (x, y, z components),
+ *   each nx*ny*nz elements, back to back (3*N floats), in voxel units unless a
+ *   call says mm.  The field u is defined on the static grid: the warped image
+ *   is W(x) = M(x + u(x)), so the static point x corresponds to the moving
+ *   point x + u(x) (the convention used to apply the field to landmarks,
+ *   Sec. 3.2).  All boundaries replicate the edge voxel.
+ *
+ * Threading and streams
+ *   A context is not thread-safe: one host thread at a time.  Every call that
+ *   takes work enqueues it on the CUDA stream given to dir_create (NULL = the
+ *   legacy default stream) and, unless it says otherwise, waits for it before
+ *   returning.  Device pointers passed in must belong to the current device.
+ *
+ * Errors
+ *   Every int-returning call returns DIR_OK (0) or a negative DIR_E* code and
+ *   never throws.  dir_last_error(ctx) describes the last failure on ctx.
+ *   After a failed dir_create, *out is NULL.
+ */
+#ifndef DIR_H
+#define DIR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIR_OK 0
+#define DIR_EINVAL (-1)   /* bad argument: NULL pointer, dims, spacing, variant, params */
+#define DIR_ENOMEM (-2)   /* device or host allocation failed */
+#define DIR_ECUDA (-3)    /* a CUDA call failed; see dir_last_error */
+#define DIR_ESTATE (-4)   /* call out of order (e.g. field requested before register) */
+#define DIR_EUNSUPPORTED (-5) /* valid request that this build does not implement */
+
+#define DIR_MAX_LEVELS 8
+#define DIR_MAX_DIM 4096              /* per axis */
+#define DIR_MAX_VOXELS (1LL << 29)    /* nx*ny*nz */
+
+typedef struct dir_ctx dir_ctx;
+
+/* The six force laws (Table 2 numbering minus one). */
+typedef enum {
+    DIR_PASSIVE = 0,            /* Eq. (1): static-image gradient, computed once per level */
+    DIR_EVOLVED_PASSIVE = 1,    /* Eq. (2): also |grad M| of the un-warped moving image */
+    DIR_ACTIVE = 2,             /* Eq. (3): gradient of the warped moving image, every iteration */
+    DIR_DOUBLE = 3,             /* Eq. (4): passive term plus active term */
+    DIR_ADJUSTED_DOUBLE = 4,    /* Eq. (5): Eq. (4) with alpha^2 d^2 in both denominators */
+    DIR_INVERSE_CONSISTENT = 5  /* Eq. (6): both images deformed toward a mid-space */
+} dir_variant;
+
+typedef enum { DIR_F32 = 0, DIR_I16 = 1, DIR_F16 = 2, DIR_BF16 = 3 } dir_dtype;
+
+typedef struct {
+    int levels;                  /* pyramid depth, 1..DIR_MAX_LEVELS (default 3; the paper uses 2, Sec. 2.3) */
+    int iters[DIR_MAX_LEVELS];   /* iterations per level, COARSEST level first (default 200, 100, 50) */
+    float sigma;                 /* Gaussian sigma in voxels (default 1.0, Sec. 2.5 "unit standard deviation");
+                                    the filter radius is ceil(3 sigma), at most 8 */
+    float alpha;                 /* Eq. (5) normalisation factor (default 0.4) */
+    int stop_mode;               /* 0: run iters exactly; 1: also stop a level when
+                                    |l(n) - l(n - stop_window)| <= eps (Sec. 2.4) */
+    double eps;                  /* default 1e-4 (Sec. 2.4) */
+    int stop_window;             /* default 10 (Sec. 2.4) */
+    dir_dtype field_dtype;       /* DIR_F32 only in this build */
+    const float* init_field;     /* NULL, or a DEVICE pointer to a level-0 field (3*N floats,
+                                    voxels) to start from; only with levels == 1 */
+    int use_graph;               /* 1 (default): capture the whole registration in a CUDA graph
+                                    on the first dir_register and replay it afterwards */
+    int timing;                  /* 1: time every force and smoothing launch at the finest level
+                                    with CUDA events (reported in dir_stats); default 0 */
+} dir_params;
+
+typedef struct {
+    int levels;
+    int iters_run[DIR_MAX_LEVELS];  /* per level, coarsest first */
+    double mse_first;               /* mean (W - S)^2 before the first iteration of the finest level */
+    double mse_final;               /* the same before the last iteration run */
+    double relnorm_final;           /* l(n) = sum|du| / sum|u| of the last iteration run (0 if undefined) */
+    float ms_total;                 /* device time of the registration (CUDA events), ms */
+    float ms_force_finest;          /* with params.timing: summed force-kernel time at level 0, ms */
+    float ms_smooth_finest;         /* with params.timing: summed smoothing-kernel time at level 0, ms */
+    int n_force_finest;             /* number of launches behind ms_force_finest */
+    int n_smooth_finest;
+    long long voxel_updates;        /* sum over levels of voxels * iterations run */
+    int kernel_launches;            /* kernels launched by the registration (incl. early exits) */
+} dir_stats;
+
+/* Fills *p with the defaults listed above.  Returns DIR_EINVAL if p is NULL. */
+int dir_params_default(dir_params* p);
+
+/*
+ * Creates a registration context for one static/moving pair.
+ *   static_img, moving_img  dense volumes of image_dtype (DIR_F32 in this build),
+ *                           host memory, or device memory if inputs_on_device != 0.
+ *                           They are copied; the caller keeps ownership.
+ *   dims                    {nx, ny, nz}, each 1..DIR_MAX_DIM, nx*ny*nz <= DIR_MAX_VOXELS
+ *   spacing_mm              voxel size, each > 0 (used only for mm output)
+ *   variant                 one of dir_variant
+ *   params                  NULL for defaults
+ *   cuda_stream             a cudaStream_t, or NULL for the legacy default stream
+ * The context owns all device memory it allocates (sized for the finest level,
+ * about 9 floats per voxel plus the pyramid).  Returns DIR_OK and sets *out, or
+ * an error and sets *out = NULL.
+ */
+int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, const int dims[3],
+               const float spacing_mm[3], dir_dtype image_dtype, int inputs_on_device,
+               dir_variant variant, const dir_params* params, void* cuda_stream);
+
+/*
+ * Replaces the image pair of ctx with new volumes of the same dims and dtype
+ * (same ownership rules as dir_create).  The field restarts from zero (or
+ * init_field) at the next dir_register.
+ */
+int dir_load(dir_ctx* ctx, const void* static_img, const void* moving_img, dir_dtype image_dtype,
+             int on_device);
+
+/*
+ * Runs the whole registration: pyramid build, then for each level (coarsest
+ * first) the field up-sampling and the iterations, then (for Eq. 6) the
+ * inversion of the mid-space field into the static-grid field.  Waits for
+ * completion and fills *stats_out if it is not NULL.
+ */
+int dir_register(dir_ctx* ctx, dir_stats* stats_out);
+
+/* Enqueues the registration on the context's stream and returns without
+   waiting.  dir_sync then waits and fills the stats. */
+int dir_register_async(dir_ctx* ctx);
+int dir_sync(dir_ctx* ctx, dir_stats* stats_out);
+
+/*
+ * Copies the registered static-grid field (3*N floats, planar, dense) to out,
+ * a host pointer or, if out_on_device != 0, a device pointer.  in_mm != 0
+ * multiplies each component by the voxel spacing of its axis.
+ * DIR_ESTATE before the first successful dir_register.
+ */
+int dir_get_field(dir_ctx* ctx, float* out, int in_mm, int out_on_device);
+
+/*
+ * Per-iteration reductions of the last registration, in the order run
+ * (coarsest level first): out[3*t + 0] = mean (W - S)^2 (for Eq. 6 the mean
+ * squared difference of the two warped images), out[3*t + 1] = sum |du|,
+ * out[3*t + 2] = sum |u| before the update, all over the voxels of the level
+ * at which iteration t ran.  Writes min(max_iters, iterations run) rows to the
+ * host array out and returns that count, or a negative error.
+ */
+int dir_get_history(dir_ctx* ctx, double* out, int max_iters);
+
+/*
+ * Warps an image on the static grid's dims by the registered field:
+ * img_out(x) = img_in(x + u(x)), trilinear, clamped (Sec. 2.5).  img_in and
+ * img_out are dense volumes of dtype dt (DIR_F32 in this build), both host or
+ * both device (on_device != 0).
+ */
+int dir_warp(dir_ctx* ctx, const void* img_in, void* img_out, dir_dtype dt, int on_device);
+
+/* Frees ctx and everything it owns.  NULL-safe. */
+void dir_destroy(dir_ctx* ctx);
+
+/* Static description of a status code. */
+const char* dir_status_string(int status);
+
+/* Description of the last failure on ctx (empty if none); ctx may be NULL for
+   the last dir_create failure of this thread. */
+const char* dir_last_error(const dir_ctx* ctx);
+
+/* Library build identifier (compute capability targeted, version). */
+const char* dir_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIR_H */

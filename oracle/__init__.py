@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-from .build import build, library_path
+from . import build as _build_mod
 
 _LIBS: dict[bool, C.CDLL] = {}
 
@@ -30,9 +30,9 @@ _ip = C.POINTER(C.c_int)
 
 def _lib(threaded: bool = False) -> C.CDLL:
     if threaded not in _LIBS:
-        path = library_path(threaded)
+        path = _build_mod.library_path(threaded)
         if not os.path.exists(path):
-            build()
+            _build_mod.build()
         lib = C.CDLL(path)
         lib.or_interp.restype = C.c_double
         lib.or_interp.argtypes = [_dp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,

@@ -1,0 +1,646 @@
+// dir_engine.cu -- registration engine and C ABI of libdir.so (see include/dir.h).
+//
+// The engine owns every device buffer of a context and issues the whole
+// registration as one stream-ordered sequence:
+//   pyramid build (Gaussian + decimation, Sec. 2.3)
+//   for each level, coarsest first:
+//     field init (zero / init_field) or up-sampling of the coarser field (Sec. 2.3)
+//     per iteration: fused force kernel (u -> v), Gaussian smoothing (v -> u),
+//                    optional relative-norm stop test (Sec. 2.4)
+//   inverse-consistent output field (Eq. 6) when that variant runs.
+// With use_graph the sequence is captured once into a CUDA graph and replayed
+// by later registrations, so the hundreds of small coarse-level launches cost
+// one graph launch.  A device-side stop flag per level lets the captured graph
+// skip the remaining iterations of a level without a host round trip.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dir.h"
+#include "dir_common.cuh"
+#include "dir_launch.h"
+
+using dirk::Grid3;
+
+namespace {
+
+constexpr int kIcInvertSteps = 20;
+constexpr int kStopUnset = 0x7f7f7f7f;  // memset byte 0x7f
+
+thread_local std::string g_create_error;
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+Grid3 make_grid(int nx, int ny, int nz) {
+    Grid3 g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.px = (int)round_up(nx, 32);
+    g.plane = (long long)g.px * ny;
+    g.cs = round_up(g.plane * nz, 64);
+    return g;
+}
+
+bool make_taps(double sigma, dirk::Taps* t) {
+    if (!(sigma > 0.0) || !isfinite(sigma)) return false;
+    const int R = (int)ceil(3.0 * sigma);
+    if (R < 1 || R > dirk::kMaxRadius) return false;
+    double w[2 * dirk::kMaxRadius + 1];
+    double sum = 0.0;
+    for (int k = -R; k <= R; ++k) {
+        w[k + R] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        sum += w[k + R];
+    }
+    t->R = R;
+    for (int k = 0; k < 17; ++k) t->w[k] = 0.0f;
+    for (int k = 0; k < 2 * R + 1; ++k) t->w[k] = (float)(w[k] / sum);
+    return true;
+}
+
+}  // namespace
+
+struct LevelBuf {
+    Grid3 g;
+    float* S;
+    float* M;
+};
+
+struct dir_ctx {
+    int dims[3];
+    float spacing[3];
+    int variant;
+    dir_params p;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int levels;
+    LevelBuf lv[DIR_MAX_LEVELS];
+    float* img_pool = nullptr;
+    float* A = nullptr;
+    float* B = nullptr;
+    double* red = nullptr;
+    double* lhist = nullptr;
+    int* ctl = nullptr;
+    int total_iters = 0;
+    int level_first[DIR_MAX_LEVELS];
+    float* final_field = nullptr;
+    bool have_field = false;
+    bool pending = false;
+    float* stage_img = nullptr;
+    float* stage_dense = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> tev;  // 3 per timed iteration: before force, between, after smooth
+    int n_timed = 0;
+    int launches = 0;
+    dirk::Taps taps, taps1;
+    std::vector<double> red_host;
+    std::vector<int> ctl_host;
+    int iters_run[DIR_MAX_LEVELS];
+    std::string err;
+};
+
+static void set_err(dir_ctx* c, const char* what, cudaError_t e) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+}
+
+#define CK(ctx, call)                       \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess) {            \
+            set_err((ctx), #call, e_);      \
+            return DIR_ECUDA;               \
+        }                                   \
+    } while (0)
+
+static int upload_pair(dir_ctx* c, const void* S, const void* M, int on_device, cudaStream_t s) {
+    const Grid3& g = c->lv[0].g;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t w = (size_t)g.nx * sizeof(float);
+    const size_t rows = (size_t)g.ny * g.nz;
+    CK(c, cudaMemcpy2DAsync(c->lv[0].S, (size_t)g.px * sizeof(float), S, w, w, rows, kind, s));
+    CK(c, cudaMemcpy2DAsync(c->lv[0].M, (size_t)g.px * sizeof(float), M, w, w, rows, kind, s));
+    return DIR_OK;
+}
+
+// Issues the whole registration on stream s (captured or direct).
+static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
+    c->launches = 0;
+    const int L = c->levels;
+    CK(c, cudaMemsetAsync(c->red, 0, sizeof(double) * 3 * (size_t)(c->total_iters > 0 ? c->total_iters : 1), s));
+    CK(c, cudaMemsetAsync(c->ctl, 0x7f, sizeof(int) * (size_t)L, s));
+
+    // pyramid (Sec. 2.3): level l+1 = unit-sigma Gaussian of level l at even indices
+    for (int l = 1; l < L; ++l) {
+        const Grid3& gf = c->lv[l - 1].g;
+        const Grid3& gc = c->lv[l].g;
+        for (int img = 0; img < 2; ++img) {
+            dirk::SmoothArgs sa;
+            sa.in = img ? c->lv[l - 1].M : c->lv[l - 1].S;
+            sa.out = c->B;
+            sa.g = gf;
+            sa.ncomp = 1;
+            sa.zchunk = dirk::smooth_zchunk(gf, c->taps1.R, c->num_sms);
+            sa.taps = c->taps1;
+            sa.stop_iter = nullptr;
+            sa.iter = 0;
+            CK(c, dirk::launch_smooth(sa, s));
+            CK(c, dirk::launch_decimate(c->B, gf, img ? c->lv[l].M : c->lv[l].S, gc, s));
+            c->launches += 2;
+        }
+    }
+
+    float* cur = c->A;
+    float* oth = c->B;
+    int row = 0;
+    c->n_timed = 0;
+    for (int lc = 0; lc < L; ++lc) {
+        const int l = L - 1 - lc;
+        const Grid3& g = c->lv[l].g;
+        if (lc == 0) {
+            if (c->p.init_field) {
+                const size_t w = (size_t)g.nx * sizeof(float);
+                const size_t n = (size_t)g.nx * g.ny * g.nz;
+                for (int comp = 0; comp < 3; ++comp)
+                    CK(c, cudaMemcpy2DAsync(cur + comp * g.cs, (size_t)g.px * sizeof(float),
+                                            c->p.init_field + comp * n, w, w,
+                                            (size_t)g.ny * g.nz, cudaMemcpyDeviceToDevice, s));
+            } else {
+                CK(c, cudaMemsetAsync(cur, 0, sizeof(float) * 3 * (size_t)g.cs, s));
+            }
+        } else {
+            CK(c, dirk::launch_upsample(cur, c->lv[l + 1].g, oth, g, s));
+            c->launches += 1;
+            float* t = cur;
+            cur = oth;
+            oth = t;
+        }
+        c->level_first[lc] = row;
+        dirk::ForceArgs fa;
+        fa.S = c->lv[l].S;
+        fa.M = c->lv[l].M;
+        fa.g = g;
+        fa.zchunk = dirk::force_zchunk(c->variant, g, c->num_sms);
+        fa.alpha2 = c->p.alpha * c->p.alpha;
+        fa.stop_iter = c->ctl + lc;
+        dirk::SmoothArgs sa;
+        sa.g = g;
+        sa.ncomp = 3;
+        sa.zchunk = dirk::smooth_zchunk(g, c->taps.R, c->num_sms);
+        sa.taps = c->taps;
+        sa.stop_iter = c->ctl + lc;
+        const bool timed = c->p.timing && l == 0;
+        for (int it = 0; it < c->p.iters[lc]; ++it, ++row) {
+            if (timed) {
+                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
+                CK(c, capturing ? cudaEventRecordWithFlags(e[0], s, cudaEventRecordExternal)
+                                : cudaEventRecord(e[0], s));
+            }
+            fa.u = cur;
+            fa.v = oth;
+            fa.red = c->red + 3 * (size_t)row;
+            fa.iter = it;
+            CK(c, dirk::launch_force(c->variant, fa, s));
+            c->launches += 1;
+            if (c->p.stop_mode == 1) {
+                CK(c, dirk::launch_stop_test(c->red, c->lhist, row, c->level_first[lc],
+                                             c->p.stop_window, c->p.eps, c->ctl + lc, it, s));
+                c->launches += 1;
+            }
+            if (timed) {
+                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
+                CK(c, capturing ? cudaEventRecordWithFlags(e[1], s, cudaEventRecordExternal)
+                                : cudaEventRecord(e[1], s));
+            }
+            sa.in = oth;
+            sa.out = cur;
+            sa.iter = it;
+            CK(c, dirk::launch_smooth(sa, s));
+            c->launches += 1;
+            if (timed) {
+                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
+                CK(c, capturing ? cudaEventRecordWithFlags(e[2], s, cudaEventRecordExternal)
+                                : cudaEventRecord(e[2], s));
+                c->n_timed += 1;
+            }
+        }
+    }
+    if (c->variant == DIR_INVERSE_CONSISTENT) {
+        CK(c, dirk::launch_ic_invert(cur, oth, c->lv[0].g, kIcInvertSteps, s));
+        c->launches += 1;
+        c->final_field = oth;
+    } else {
+        c->final_field = cur;
+    }
+    return DIR_OK;
+}
+
+static int capture_graph(dir_ctx* c) {
+    CK(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_registration(c, c->cap, true);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap, &graph);
+    if (rc != DIR_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        set_err(c, "cudaStreamEndCapture", e);
+        return DIR_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        set_err(c, "cudaGraphInstantiate", ei);
+        c->exec = nullptr;
+        return DIR_ECUDA;
+    }
+    return DIR_OK;
+}
+
+static void release(dir_ctx* c) {
+    if (!c) return;
+    if (c->stream || c->cap) cudaStreamSynchronize(c->stream);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    cudaFree(c->img_pool);
+    cudaFree(c->A);
+    cudaFree(c->B);
+    cudaFree(c->red);
+    cudaFree(c->lhist);
+    cudaFree(c->ctl);
+    cudaFree(c->stage_img);
+    cudaFree(c->stage_dense);
+    delete c;
+}
+
+static int validate_params(const dir_params* p) {
+    if (p->levels < 1 || p->levels > DIR_MAX_LEVELS) return DIR_EINVAL;
+    for (int l = 0; l < p->levels; ++l)
+        if (p->iters[l] < 0 || p->iters[l] > 1000000) return DIR_EINVAL;
+    dirk::Taps t;
+    if (!make_taps(p->sigma, &t)) return DIR_EINVAL;
+    if (!isfinite(p->alpha)) return DIR_EINVAL;
+    if (p->stop_mode != 0 && p->stop_mode != 1) return DIR_EINVAL;
+    if (p->stop_mode == 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
+    if (p->field_dtype != DIR_F32) return DIR_EUNSUPPORTED;
+    if (p->init_field && p->levels != 1) return DIR_EINVAL;
+    return DIR_OK;
+}
+
+extern "C" {
+
+int dir_params_default(dir_params* p) {
+    if (!p) return DIR_EINVAL;
+    memset(p, 0, sizeof *p);
+    p->levels = 3;
+    p->iters[0] = 200;
+    p->iters[1] = 100;
+    p->iters[2] = 50;
+    p->sigma = 1.0f;
+    p->alpha = 0.4f;
+    p->stop_mode = 0;
+    p->eps = 1e-4;
+    p->stop_window = 10;
+    p->field_dtype = DIR_F32;
+    p->init_field = nullptr;
+    p->use_graph = 1;
+    p->timing = 0;
+    return DIR_OK;
+}
+
+int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, const int dims[3],
+               const float spacing_mm[3], dir_dtype image_dtype, int inputs_on_device,
+               dir_variant variant, const dir_params* params, void* cuda_stream) {
+    g_create_error.clear();
+    if (!out) return DIR_EINVAL;
+    *out = nullptr;
+    if (!static_img || !moving_img || !dims || !spacing_mm) {
+        g_create_error = "NULL argument";
+        return DIR_EINVAL;
+    }
+    long long nvox = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > DIR_MAX_DIM || !(spacing_mm[a] > 0.0f) ||
+            !isfinite(spacing_mm[a])) {
+            g_create_error = "bad dims or spacing";
+            return DIR_EINVAL;
+        }
+        nvox *= dims[a];
+    }
+    if (nvox > DIR_MAX_VOXELS) {
+        g_create_error = "volume too large";
+        return DIR_EINVAL;
+    }
+    if ((int)variant < 0 || (int)variant > 5) {
+        g_create_error = "bad variant";
+        return DIR_EINVAL;
+    }
+    if (image_dtype != DIR_F32) {
+        g_create_error = "image dtype not supported by this build";
+        return DIR_EUNSUPPORTED;
+    }
+    dir_params p;
+    if (params)
+        p = *params;
+    else
+        dir_params_default(&p);
+    const int prc = validate_params(&p);
+    if (prc != DIR_OK) {
+        g_create_error = "bad params";
+        return prc;
+    }
+
+    dir_ctx* c = new (std::nothrow) dir_ctx();
+    if (!c) return DIR_ENOMEM;
+    for (int a = 0; a < 3; ++a) {
+        c->dims[a] = dims[a];
+        c->spacing[a] = spacing_mm[a];
+    }
+    c->variant = (int)variant;
+    c->p = p;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->levels = p.levels;
+    make_taps(p.sigma, &c->taps);
+    make_taps(1.0, &c->taps1);
+
+    int rc = DIR_OK;
+    auto fail = [&](int code) {
+        if (g_create_error.empty()) g_create_error = c->err;
+        release(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        set_err(c, "cudaGetDevice", e);
+        return fail(DIR_ECUDA);
+    }
+
+    // level grids and one pool for all pyramid images
+    int nx = dims[0], ny = dims[1], nz = dims[2];
+    size_t pool = 0;
+    for (int l = 0; l < c->levels; ++l) {
+        c->lv[l].g = make_grid(nx, ny, nz);
+        pool += 2 * (size_t)c->lv[l].g.cs;
+        nx = (nx + 1) / 2;
+        ny = (ny + 1) / 2;
+        nz = (nz + 1) / 2;
+    }
+    const size_t field = 3 * (size_t)c->lv[0].g.cs;
+    c->total_iters = 0;
+    for (int l = 0; l < c->levels; ++l) c->total_iters += p.iters[l];
+    const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
+    if (cudaMalloc(&c->img_pool, pool * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->A, field * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->B, field * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->red, 3 * nred * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->lhist, nred * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->ctl, DIR_MAX_LEVELS * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "device allocation failed";
+        return fail(DIR_ENOMEM);
+    }
+    size_t at = 0;
+    for (int l = 0; l < c->levels; ++l) {
+        c->lv[l].S = c->img_pool + at;
+        at += c->lv[l].g.cs;
+        c->lv[l].M = c->img_pool + at;
+        at += c->lv[l].g.cs;
+    }
+    e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e != cudaSuccess) {
+        set_err(c, "stream/event creation", e);
+        return fail(DIR_ECUDA);
+    }
+    if (p.timing) {
+        const int n = p.iters[c->levels - 1];
+        c->tev.resize(3 * (size_t)n, nullptr);
+        for (auto& ev : c->tev) {
+            e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) {
+                set_err(c, "cudaEventCreate", e);
+                return fail(DIR_ECUDA);
+            }
+        }
+    }
+    e = cudaMemsetAsync(c->img_pool, 0, pool * sizeof(float), c->stream);
+    if (e != cudaSuccess) {
+        set_err(c, "cudaMemsetAsync", e);
+        return fail(DIR_ECUDA);
+    }
+    rc = upload_pair(c, static_img, moving_img, inputs_on_device, c->stream);
+    if (rc != DIR_OK) return fail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        set_err(c, "cudaStreamSynchronize", e);
+        return fail(DIR_ECUDA);
+    }
+    *out = c;
+    return DIR_OK;
+}
+
+int dir_load(dir_ctx* c, const void* S, const void* M, dir_dtype dt, int on_device) {
+    if (!c || !S || !M) return DIR_EINVAL;
+    if (dt != DIR_F32) return DIR_EUNSUPPORTED;
+    if (c->pending) return DIR_ESTATE;
+    const int rc = upload_pair(c, S, M, on_device, c->stream);
+    if (rc != DIR_OK) return rc;
+    c->have_field = false;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DIR_OK;
+}
+
+int dir_register_async(dir_ctx* c) {
+    if (!c) return DIR_EINVAL;
+    if (c->pending) return DIR_ESTATE;
+    if (c->p.use_graph && !c->exec) {
+        const int rc = capture_graph(c);
+        if (rc != DIR_OK) return rc;
+    }
+    CK(c, cudaEventRecord(c->ev0, c->stream));
+    if (c->p.use_graph) {
+        CK(c, cudaGraphLaunch(c->exec, c->stream));
+    } else {
+        const int rc = enqueue_registration(c, c->stream, false);
+        if (rc != DIR_OK) return rc;
+    }
+    CK(c, cudaEventRecord(c->ev1, c->stream));
+    c->pending = true;
+    c->have_field = false;
+    return DIR_OK;
+}
+
+int dir_sync(dir_ctx* c, dir_stats* st) {
+    if (!c) return DIR_EINVAL;
+    if (!c->pending) return DIR_ESTATE;
+    c->pending = false;
+    const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
+    c->red_host.resize(3 * nred);
+    c->ctl_host.resize(DIR_MAX_LEVELS);
+    CK(c, cudaMemcpyAsync(c->red_host.data(), c->red, 3 * nred * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->ctl_host.data(), c->ctl, c->levels * sizeof(int),
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->have_field = true;
+    long long vu = 0;
+    for (int lc = 0; lc < c->levels; ++lc) {
+        const int stop = c->ctl_host[lc];
+        int run = c->p.iters[lc];
+        if (stop != kStopUnset && stop + 1 < run) run = stop + 1;
+        c->iters_run[lc] = run;
+        const Grid3& g = c->lv[c->levels - 1 - lc].g;
+        vu += (long long)g.nx * g.ny * g.nz * run;
+    }
+    if (st) {
+        memset(st, 0, sizeof *st);
+        st->levels = c->levels;
+        for (int lc = 0; lc < c->levels; ++lc) st->iters_run[lc] = c->iters_run[lc];
+        const int fin = c->levels - 1;
+        const Grid3& g0 = c->lv[0].g;
+        const double n0 = (double)g0.nx * g0.ny * g0.nz;
+        if (c->iters_run[fin] > 0) {
+            const int r0 = c->level_first[fin];
+            const int r1 = r0 + c->iters_run[fin] - 1;
+            st->mse_first = c->red_host[3 * r0] / n0;
+            st->mse_final = c->red_host[3 * r1] / n0;
+            const double B = c->red_host[3 * r1 + 2];
+            st->relnorm_final = B > 0.0 ? c->red_host[3 * r1 + 1] / B : 0.0;
+        }
+        float ms = 0.0f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        st->ms_total = ms;
+        st->voxel_updates = vu;
+        st->kernel_launches = c->launches;
+        if (c->p.timing) {
+            const int runs = c->iters_run[fin];
+            for (int i = 0; i < c->n_timed && i < runs; ++i) {
+                float a = 0.f, b = 0.f;
+                CK(c, cudaEventElapsedTime(&a, c->tev[3 * i], c->tev[3 * i + 1]));
+                CK(c, cudaEventElapsedTime(&b, c->tev[3 * i + 1], c->tev[3 * i + 2]));
+                st->ms_force_finest += a;
+                st->ms_smooth_finest += b;
+                st->n_force_finest += 1;
+                st->n_smooth_finest += 1;
+            }
+        }
+    }
+    return DIR_OK;
+}
+
+int dir_register(dir_ctx* c, dir_stats* st) {
+    const int rc = dir_register_async(c);
+    if (rc != DIR_OK) return rc;
+    return dir_sync(c, st);
+}
+
+int dir_get_history(dir_ctx* c, double* out, int max_iters) {
+    if (!c || (!out && max_iters > 0) || max_iters < 0) return DIR_EINVAL;
+    if (!c->have_field) return DIR_ESTATE;
+    int w = 0;
+    for (int lc = 0; lc < c->levels; ++lc) {
+        const Grid3& g = c->lv[c->levels - 1 - lc].g;
+        const double n = (double)g.nx * g.ny * g.nz;
+        for (int it = 0; it < c->iters_run[lc] && w < max_iters; ++it, ++w) {
+            const double* r = &c->red_host[3 * (size_t)(c->level_first[lc] + it)];
+            out[3 * w + 0] = r[0] / n;
+            out[3 * w + 1] = r[1];
+            out[3 * w + 2] = r[2];
+        }
+    }
+    return w;
+}
+
+int dir_get_field(dir_ctx* c, float* out, int in_mm, int out_on_device) {
+    if (!c || !out) return DIR_EINVAL;
+    if (!c->have_field || !c->final_field) return DIR_ESTATE;
+    const Grid3& g = c->lv[0].g;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    float* dst = out;
+    if (!out_on_device) {
+        if (!c->stage_dense && cudaMalloc(&c->stage_dense, 3 * n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            c->stage_dense = nullptr;
+            return DIR_ENOMEM;
+        }
+        dst = c->stage_dense;
+    }
+    const float sx = in_mm ? c->spacing[0] : 1.0f;
+    const float sy = in_mm ? c->spacing[1] : 1.0f;
+    const float sz = in_mm ? c->spacing[2] : 1.0f;
+    CK(c, dirk::launch_export_field(c->final_field, g, sx, sy, sz, dst, c->stream));
+    if (!out_on_device)
+        CK(c, cudaMemcpyAsync(out, dst, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DIR_OK;
+}
+
+int dir_warp(dir_ctx* c, const void* img_in, void* img_out, dir_dtype dt, int on_device) {
+    if (!c || !img_in || !img_out) return DIR_EINVAL;
+    if (dt != DIR_F32) return DIR_EUNSUPPORTED;
+    if (!c->have_field || !c->final_field) return DIR_ESTATE;
+    const Grid3& g = c->lv[0].g;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    if (!c->stage_img && cudaMalloc(&c->stage_img, (size_t)g.cs * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        c->stage_img = nullptr;
+        return DIR_ENOMEM;
+    }
+    const size_t w = (size_t)g.nx * sizeof(float);
+    CK(c, cudaMemcpy2DAsync(c->stage_img, (size_t)g.px * sizeof(float), img_in, w, w,
+                            (size_t)g.ny * g.nz,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            c->stream));
+    float* dst = (float*)img_out;
+    if (!on_device) {
+        if (!c->stage_dense && cudaMalloc(&c->stage_dense, 3 * n * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            c->stage_dense = nullptr;
+            return DIR_ENOMEM;
+        }
+        dst = c->stage_dense;
+    }
+    CK(c, dirk::launch_warp(c->stage_img, c->final_field, g, dst, c->stream));
+    if (!on_device)
+        CK(c, cudaMemcpyAsync(img_out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return DIR_OK;
+}
+
+void dir_destroy(dir_ctx* c) { release(c); }
+
+const char* dir_status_string(int s) {
+    switch (s) {
+        case DIR_OK: return "ok";
+        case DIR_EINVAL: return "invalid argument";
+        case DIR_ENOMEM: return "out of memory";
+        case DIR_ECUDA: return "CUDA error";
+        case DIR_ESTATE: return "call out of order";
+        case DIR_EUNSUPPORTED: return "not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+const char* dir_last_error(const dir_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+const char* dir_version(void) { return "gb300-demons 0.1 (sm_103a)"; }
+
+}  // extern "C"

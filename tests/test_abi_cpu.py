@@ -1,0 +1,92 @@
+"""The C-ABI library loads and exports every symbol include/dir.h declares;
+host-side argument checks run without a GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "dir.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dir_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def dl():
+    import paper_0909_0928_gb300 as dl
+    return dl
+
+
+def test_library_exports_every_declared_symbol(dl):
+    declared = _declared_symbols()
+    assert len(declared) >= 13
+    lib = C.CDLL(dl.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(dl.EXPORTS) == declared
+
+
+def test_params_default_and_status_strings(dl):
+    p = dl.dir_params_default()
+    assert p.levels == 3 and list(p.iters[:3]) == [200, 100, 50]
+    assert p.sigma == 1.0 and abs(p.alpha - 0.4) < 1e-7
+    assert p.eps == 1e-4 and p.stop_window == 10 and p.use_graph == 1
+    assert dl.dir_status_string(0) == "ok"
+    assert dl.dir_status_string(dl.DIR_EINVAL) == "invalid argument"
+    assert "sm_103a" in dl.dir_version()
+
+
+def test_struct_layouts_match_header(dl, tmp_path):
+    # compile a probe against include/dir.h and compare every field offset
+    fields = {"dir_params": [f for f, _ in dl.DirParams._fields_],
+              "dir_stats": [f for f, _ in dl.DirStats._fields_]}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dir.h"', "int main(void){"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "probe"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.split("\n") if line)
+    for st, cls in (("dir_params", dl.DirParams), ("dir_stats", dl.DirStats)):
+        assert int(out[st]) == C.sizeof(cls), st
+        for f in fields[st]:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_argument_checks_precede_device_work(dl):
+    S = np.zeros((4, 4, 4), np.float32)
+    with pytest.raises(dl.DirError) as e:
+        dl.dir_create(S, S, (4, 4, 0), (1, 1, 1))
+    assert e.value.code == dl.DIR_EINVAL
+    with pytest.raises(dl.DirError) as e:
+        dl.dir_create(S, S, (4, 4, 4), (1, -1, 1))
+    assert e.value.code == dl.DIR_EINVAL
+    with pytest.raises(dl.DirError) as e:
+        dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), variant=6)
+    assert e.value.code == dl.DIR_EINVAL
+    with pytest.raises(dl.DirError) as e:
+        dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), image_dtype=dl.DIR_I16)
+    assert e.value.code == dl.DIR_EUNSUPPORTED
+    for bad in (dict(levels=0), dict(levels=9), dict(sigma=0.0), dict(sigma=3.0),
+                dict(stop_mode=1, stop_window=0), dict(iters=[-1, 1, 1])):
+        p = dl.dir_params_default(**bad)
+        with pytest.raises(dl.DirError) as e:
+            dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), params=p)
+        assert e.value.code == dl.DIR_EINVAL, bad
+
+
+def test_null_safe_destroy(dl):
+    dl._lib.dir_destroy(None)
