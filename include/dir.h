@@ -46,6 +46,8 @@ extern "C" {
 #define DIR_ECUDA (-3)    /* a CUDA call failed; see dir_last_error */
 #define DIR_ESTATE (-4)   /* call out of order (e.g. field requested before register) */
 #define DIR_EUNSUPPORTED (-5) /* valid request that this build does not implement */
+#define DIR_ETIMEOUT (-6)  /* a bounded device-side wait gave up (data copy never landed);
+                              the context's results are invalid */
 
 #define DIR_MAX_LEVELS 8
 #define DIR_MAX_DIM 4096              /* per axis */
@@ -63,7 +65,7 @@ typedef enum {
     DIR_INVERSE_CONSISTENT = 5  /* Eq. (6): both images deformed toward a mid-space */
 } dir_variant;
 
-typedef enum { DIR_F32 = 0, DIR_I16 = 1, DIR_F16 = 2, DIR_BF16 = 3 } dir_dtype;
+typedef enum { DIR_F32 = 0, DIR_I16 = 1, DIR_F16 = 2, DIR_BF16 = 3, DIR_F64 = 4 } dir_dtype;
 
 typedef struct {
     int levels;                  /* pyramid depth, 1..DIR_MAX_LEVELS (default 3; the paper uses 2, Sec. 2.3) */
@@ -82,6 +84,10 @@ typedef struct {
                                     on the first dir_register and replay it afterwards */
     int timing;                  /* 1: time every force and smoothing launch at the finest level
                                     with CUDA events (reported in dir_stats); default 0 */
+    dir_dtype precision;         /* arithmetic and storage of images and fields on the device:
+                                    DIR_F32 (default, the production path) or DIR_F64 (the same
+                                    kernels in double precision, for verification against an
+                                    FP64 reference where the iteration is ill-conditioned) */
 } dir_params;
 
 typedef struct {
@@ -148,6 +154,9 @@ int dir_sync(dir_ctx* ctx, dir_stats* stats_out);
  * DIR_ESTATE before the first successful dir_register.
  */
 int dir_get_field(dir_ctx* ctx, float* out, int in_mm, int out_on_device);
+
+/* As dir_get_field, but writes doubles (exact for DIR_F64 contexts). */
+int dir_get_field_f64(dir_ctx* ctx, double* out, int in_mm, int out_on_device);
 
 /*
  * Per-iteration reductions of the last registration, in the order run

@@ -7,8 +7,8 @@ kernels.  There is no CPU fallback: if libdir.so is missing or fails to load,
 importing this package raises.
 
 Functions carry the C names: dir_params_default, dir_create, dir_load,
-dir_register, dir_register_async, dir_sync, dir_get_field, dir_get_history,
-dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version.
+dir_register, dir_register_async, dir_sync, dir_get_field, dir_get_field_f64,
+dir_get_history, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version.
 `Registration` wraps a context for convenience.
 """
 from __future__ import annotations
@@ -21,17 +21,18 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdir.so")
 
-DIR_OK, DIR_EINVAL, DIR_ENOMEM, DIR_ECUDA, DIR_ESTATE, DIR_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DIR_OK, DIR_EINVAL, DIR_ENOMEM, DIR_ECUDA, DIR_ESTATE, DIR_EUNSUPPORTED, DIR_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6)
 DIR_MAX_LEVELS = 8
 (DIR_PASSIVE, DIR_EVOLVED_PASSIVE, DIR_ACTIVE, DIR_DOUBLE, DIR_ADJUSTED_DOUBLE,
  DIR_INVERSE_CONSISTENT) = range(6)
-DIR_F32, DIR_I16, DIR_F16, DIR_BF16 = range(4)
+DIR_F32, DIR_I16, DIR_F16, DIR_BF16, DIR_F64 = range(5)
 VARIANTS = {"passive": 0, "evolved_passive": 1, "active": 2, "double": 3, "adjusted_double": 4,
             "inverse_consistent": 5}
 
 # every symbol the C header declares
 EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_register_async",
-           "dir_sync", "dir_get_field", "dir_get_history", "dir_warp", "dir_destroy",
+           "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history", "dir_warp", "dir_destroy",
            "dir_status_string", "dir_last_error", "dir_version"]
 
 
@@ -39,7 +40,8 @@ class DirParams(C.Structure):
     _fields_ = [("levels", C.c_int), ("iters", C.c_int * DIR_MAX_LEVELS), ("sigma", C.c_float),
                 ("alpha", C.c_float), ("stop_mode", C.c_int), ("eps", C.c_double),
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
-                ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int)]
+                ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
+                ("precision", C.c_int)]
 
 
 class DirStats(C.Structure):
@@ -81,6 +83,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_register_async": (ip, [vp]),
         "dir_sync": (ip, [vp, C.POINTER(DirStats)]),
         "dir_get_field": (ip, [vp, vp, ip, ip]),
+        "dir_get_field_f64": (ip, [vp, vp, ip, ip]),
         "dir_get_history": (ip, [vp, C.POINTER(C.c_double), ip]),
         "dir_warp": (ip, [vp, vp, vp, ip, ip]),
         "dir_destroy": (None, [vp]),
@@ -208,6 +211,13 @@ def dir_get_field(ctx, out, in_mm=False, out_on_device=False):
     return out
 
 
+def dir_get_field_f64(ctx, out, in_mm=False, out_on_device=False):
+    """As dir_get_field with a float64 `out` (numpy or torch CUDA tensor)."""
+    _check(_lib.dir_get_field_f64(ctx, _ptr(out, out_on_device), int(bool(in_mm)),
+                                  int(bool(out_on_device))), "dir_get_field_f64", ctx)
+    return out
+
+
 def dir_get_history(ctx, max_iters: int) -> np.ndarray:
     buf = np.zeros((max(int(max_iters), 0), 3), dtype=np.float64)
     n = _check(_lib.dir_get_history(ctx, buf.ctypes.data_as(C.POINTER(C.c_double)),
@@ -247,12 +257,13 @@ class Registration:
         self.stats = dir_register(self.ctx)
         return self.stats
 
-    def field(self, in_mm=False, out=None):
+    def field(self, in_mm=False, out=None, f64=False):
         nx, ny, nz = self.dims
         if out is None:
-            out = np.empty((3, nz, ny, nx), dtype=np.float32)
+            out = np.empty((3, nz, ny, nx), dtype=np.float64 if f64 else np.float32)
         on_dev = _is_torch(out) and bool(out.is_cuda)
-        dir_get_field(self.ctx, out, in_mm, on_dev)
+        is64 = (str(out.dtype).endswith("float64"))
+        (dir_get_field_f64 if is64 else dir_get_field)(self.ctx, out, in_mm, on_dev)
         return out
 
     def history(self) -> np.ndarray:

@@ -1,11 +1,15 @@
 // dir_common.cuh -- device-side layout and helpers shared by the library's kernels.
 //
 // Internal volumes are pitched: voxel (i, j, k) of a level lives at
-// i + px * j + plane * k with px >= nx a multiple of 32 floats and
+// i + px * j + plane * k with px >= nx a multiple of 32 elements and
 // plane = px * ny, so every row starts on a 128-byte boundary.  A field stores
-// its three components cs floats apart (cs a multiple of 64).
+// its three components cs elements apart (cs a multiple of 64).
+//
+// Every kernel is a template on the scalar type Real (float for production,
+// double for the verification precision); the arithmetic is written once.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -13,17 +17,20 @@ namespace dirk {
 
 struct Grid3 {
     int nx, ny, nz;   // voxels per axis
-    int px;           // row pitch in floats
+    int px;           // row pitch in elements
     long long plane;  // px * ny
-    long long cs;     // component stride of a field, floats
+    long long cs;     // component stride of a field, elements
 };
 
 struct Taps {
-    int R;         // radius: 2R+1 taps
-    float w[17];   // w[t + R] for t = -R..R
+    int R;          // radius: 2R+1 taps
+    double w[17];   // w[t + R] for t = -R..R (normalised)
 };
 
 constexpr int kMaxRadius = 8;
+
+// error bits a kernel can raise in the context's device error word
+constexpr int kErrTmaTimeout = 1;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -31,52 +38,60 @@ __device__ __forceinline__ long long offs(const Grid3& g, int i, int j, int k) {
     return (long long)i + (long long)g.px * j + g.plane * k;
 }
 
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double r_floor(double x) { return floor(x); }
+__device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+__device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
 // One axis of the trilinear setup (Sec. 2.5 interpolation, clamped
 // coordinates): lower corner floor(p) kept <= n-2 so the upper corner exists.
-__device__ __forceinline__ void axis_setup(float p, int n, int& i0, int& i1, float& f) {
-    p = fminf(fmaxf(p, 0.0f), (float)(n - 1));
-    int lo = (int)floorf(p);
+template <typename Real>
+__device__ __forceinline__ void axis_setup(Real p, int n, int& i0, int& i1, Real& f) {
+    p = r_clamp(p, Real(0), Real(n - 1));
+    int lo = (int)r_floor(p);
     lo = min(lo, n - 2);
     lo = max(lo, 0);
     i0 = lo;
     i1 = (n > 1) ? lo + 1 : lo;
-    f = p - (float)lo;
+    f = p - (Real)lo;
 }
 
 // Software trilinear interpolation of a pitched volume at a continuous voxel
 // position (x, y, z); lerps along x, then y, then z.
-__device__ __forceinline__ float trilinear(const float* __restrict__ I, const Grid3& g, float x,
-                                           float y, float z) {
+template <typename Real>
+__device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid3& g, Real x,
+                                          Real y, Real z) {
     int x0, x1, y0, y1, z0, z1;
-    float fx, fy, fz;
+    Real fx, fy, fz;
     axis_setup(x, g.nx, x0, x1, fx);
     axis_setup(y, g.ny, y0, y1, fy);
     axis_setup(z, g.nz, z0, z1, fz);
-    const float* p00 = I + (long long)g.px * y0 + g.plane * z0;
-    const float* p10 = I + (long long)g.px * y1 + g.plane * z0;
-    const float* p01 = I + (long long)g.px * y0 + g.plane * z1;
-    const float* p11 = I + (long long)g.px * y1 + g.plane * z1;
-    const float c000 = __ldg(p00 + x0), c100 = __ldg(p00 + x1);
-    const float c010 = __ldg(p10 + x0), c110 = __ldg(p10 + x1);
-    const float c001 = __ldg(p01 + x0), c101 = __ldg(p01 + x1);
-    const float c011 = __ldg(p11 + x0), c111 = __ldg(p11 + x1);
-    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
-    const float v00 = c000 * gx + c100 * fx;
-    const float v10 = c010 * gx + c110 * fx;
-    const float v01 = c001 * gx + c101 * fx;
-    const float v11 = c011 * gx + c111 * fx;
-    const float v0 = v00 * gy + v10 * fy;
-    const float v1 = v01 * gy + v11 * fy;
+    const Real* p00 = I + (long long)g.px * y0 + g.plane * z0;
+    const Real* p10 = I + (long long)g.px * y1 + g.plane * z0;
+    const Real* p01 = I + (long long)g.px * y0 + g.plane * z1;
+    const Real* p11 = I + (long long)g.px * y1 + g.plane * z1;
+    const Real c000 = __ldg(p00 + x0), c100 = __ldg(p00 + x1);
+    const Real c010 = __ldg(p10 + x0), c110 = __ldg(p10 + x1);
+    const Real c001 = __ldg(p01 + x0), c101 = __ldg(p01 + x1);
+    const Real c011 = __ldg(p11 + x0), c111 = __ldg(p11 + x1);
+    const Real gx = Real(1) - fx, gy = Real(1) - fy, gz = Real(1) - fz;
+    const Real v00 = c000 * gx + c100 * fx;
+    const Real v10 = c010 * gx + c110 * fx;
+    const Real v01 = c001 * gx + c101 * fx;
+    const Real v11 = c011 * gx + c111 * fx;
+    const Real v0 = v00 * gy + v10 * fy;
+    const Real v1 = v01 * gy + v11 * fy;
     return v0 * gz + v1 * fz;
 }
 
 // Block-wide sum of three per-thread values in double, then one FP64 atomic
 // per value.  Every thread of the block must call it.
 template <int NT>
-__device__ __forceinline__ void block_reduce3_atomic(float a, float b, float c, double* out) {
+__device__ __forceinline__ void block_reduce3_atomic(double da, double db, double dc, double* out) {
     static_assert(NT % 32 == 0, "block size must be whole warps");
     __shared__ double red_s[3][NT / 32];
-    double da = a, db = b, dc = c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         da += __shfl_down_sync(0xffffffffu, da, o);
@@ -107,6 +122,74 @@ __device__ __forceinline__ void block_reduce3_atomic(float a, float b, float c, 
             atomicAdd(out + 2, dc);
         }
     }
+}
+
+// ---------------------------------------------------------------- TMA / mbarrier
+// Bulk tensor copies (cp.async.bulk.tensor) complete on an mbarrier in shared
+// memory; waits are bounded by the global timer so that a copy that never
+// lands raises an error instead of hanging the GPU.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the barrier; gives up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// 4-D tiled tensor load global -> shared, completing on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
 }
 
 }  // namespace dirk

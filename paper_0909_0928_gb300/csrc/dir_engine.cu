@@ -12,6 +12,8 @@
 // by later registrations, so the hundreds of small coarse-level launches cost
 // one graph launch.  A device-side stop flag per level lets the captured graph
 // skip the remaining iterations of a level without a host round trip.
+// Images and fields live on the device as float (DIR_F32) or double (DIR_F64);
+// the same kernel templates serve both.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -58,8 +60,8 @@ bool make_taps(double sigma, dirk::Taps* t) {
         sum += w[k + R];
     }
     t->R = R;
-    for (int k = 0; k < 17; ++k) t->w[k] = 0.0f;
-    for (int k = 0; k < 2 * R + 1; ++k) t->w[k] = (float)(w[k] / sum);
+    for (int k = 0; k < 17; ++k) t->w[k] = 0.0;
+    for (int k = 0; k < 2 * R + 1; ++k) t->w[k] = w[k] / sum;
     return true;
 }
 
@@ -67,8 +69,8 @@ bool make_taps(double sigma, dirk::Taps* t) {
 
 struct LevelBuf {
     Grid3 g;
-    float* S;
-    float* M;
+    char* S;
+    char* M;
 };
 
 struct dir_ctx {
@@ -76,24 +78,28 @@ struct dir_ctx {
     float spacing[3];
     int variant;
     dir_params p;
+    bool fp64;
+    size_t esz;
     cudaStream_t stream;
     int device;
     int num_sms;
     int levels;
     LevelBuf lv[DIR_MAX_LEVELS];
-    float* img_pool = nullptr;
-    float* A = nullptr;
-    float* B = nullptr;
+    char* img_pool = nullptr;
+    char* A = nullptr;
+    char* B = nullptr;
     double* red = nullptr;
     double* lhist = nullptr;
     int* ctl = nullptr;
+    int* derr = nullptr;
     int total_iters = 0;
     int level_first[DIR_MAX_LEVELS];
-    float* final_field = nullptr;
+    char* final_field = nullptr;
     bool have_field = false;
     bool pending = false;
-    float* stage_img = nullptr;
-    float* stage_dense = nullptr;
+    char* stage_img = nullptr;      // pitched, element type of the context
+    float* stage_f32 = nullptr;     // dense float, 3*N
+    double* stage_f64 = nullptr;    // dense double, 3*N
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -105,6 +111,8 @@ struct dir_ctx {
     std::vector<int> ctl_host;
     int iters_run[DIR_MAX_LEVELS];
     std::string err;
+
+    size_t nvox() const { return (size_t)dims[0] * dims[1] * dims[2]; }
 };
 
 static void set_err(dir_ctx* c, const char* what, cudaError_t e) {
@@ -125,13 +133,51 @@ static void set_err(dir_ctx* c, const char* what, cudaError_t e) {
         }                                   \
     } while (0)
 
+static int ensure(dir_ctx* c, void** p, size_t bytes) {
+    if (*p) return DIR_OK;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        c->err = "device allocation failed";
+        return DIR_ENOMEM;
+    }
+    return DIR_OK;
+}
+
+// dense float volume(s) (host or device) -> pitched volume(s) of the context type
+static int import_dense(dir_ctx* c, const float* src, int on_device, char* dst, const Grid3& g,
+                        int ncomp, cudaStream_t s) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    if (!c->fp64) {
+        const size_t w = (size_t)g.nx * sizeof(float);
+        for (int comp = 0; comp < ncomp; ++comp)
+            CK(c, cudaMemcpy2DAsync(dst + comp * g.cs * c->esz, (size_t)g.px * sizeof(float),
+                                    src + comp * n, w, w, (size_t)g.ny * g.nz,
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    s));
+        return DIR_OK;
+    }
+    const float* dsrc = src;
+    if (!on_device) {
+        const int rc = ensure(c, (void**)&c->stage_f32, 3 * n * sizeof(float));
+        if (rc != DIR_OK) return rc;
+        CK(c, cudaMemcpyAsync(c->stage_f32, src, ncomp * n * sizeof(float), cudaMemcpyHostToDevice,
+                              s));
+        dsrc = c->stage_f32;
+    }
+    CK(c, dirk::launch_import(true, dsrc, dst, g, ncomp, s));
+    return DIR_OK;
+}
+
 static int upload_pair(dir_ctx* c, const void* S, const void* M, int on_device, cudaStream_t s) {
-    const Grid3& g = c->lv[0].g;
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const size_t w = (size_t)g.nx * sizeof(float);
-    const size_t rows = (size_t)g.ny * g.nz;
-    CK(c, cudaMemcpy2DAsync(c->lv[0].S, (size_t)g.px * sizeof(float), S, w, w, rows, kind, s));
-    CK(c, cudaMemcpy2DAsync(c->lv[0].M, (size_t)g.px * sizeof(float), M, w, w, rows, kind, s));
+    int rc = import_dense(c, (const float*)S, on_device, c->lv[0].S, c->lv[0].g, 1, s);
+    if (rc == DIR_OK) rc = import_dense(c, (const float*)M, on_device, c->lv[0].M, c->lv[0].g, 1, s);
+    return rc;
+}
+
+static int record(dir_ctx* c, cudaEvent_t e, cudaStream_t s, bool capturing) {
+    CK(c, capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                    : cudaEventRecord(e, s));
     return DIR_OK;
 }
 
@@ -139,8 +185,10 @@ static int upload_pair(dir_ctx* c, const void* S, const void* M, int on_device, 
 static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
     c->launches = 0;
     const int L = c->levels;
+    const bool f64 = c->fp64;
     CK(c, cudaMemsetAsync(c->red, 0, sizeof(double) * 3 * (size_t)(c->total_iters > 0 ? c->total_iters : 1), s));
     CK(c, cudaMemsetAsync(c->ctl, 0x7f, sizeof(int) * (size_t)L, s));
+    CK(c, cudaMemsetAsync(c->derr, 0, sizeof(int), s));
 
     // pyramid (Sec. 2.3): level l+1 = unit-sigma Gaussian of level l at even indices
     for (int l = 1; l < L; ++l) {
@@ -152,18 +200,18 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.out = c->B;
             sa.g = gf;
             sa.ncomp = 1;
-            sa.zchunk = dirk::smooth_zchunk(gf, c->taps1.R, c->num_sms);
             sa.taps = c->taps1;
             sa.stop_iter = nullptr;
             sa.iter = 0;
-            CK(c, dirk::launch_smooth(sa, s));
-            CK(c, dirk::launch_decimate(c->B, gf, img ? c->lv[l].M : c->lv[l].S, gc, s));
+            sa.err = c->derr;
+            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
+            CK(c, dirk::launch_decimate(f64, c->B, gf, img ? c->lv[l].M : c->lv[l].S, gc, s));
             c->launches += 2;
         }
     }
 
-    float* cur = c->A;
-    float* oth = c->B;
+    char* cur = c->A;
+    char* oth = c->B;
     int row = 0;
     c->n_timed = 0;
     for (int lc = 0; lc < L; ++lc) {
@@ -171,19 +219,16 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         const Grid3& g = c->lv[l].g;
         if (lc == 0) {
             if (c->p.init_field) {
-                const size_t w = (size_t)g.nx * sizeof(float);
-                const size_t n = (size_t)g.nx * g.ny * g.nz;
-                for (int comp = 0; comp < 3; ++comp)
-                    CK(c, cudaMemcpy2DAsync(cur + comp * g.cs, (size_t)g.px * sizeof(float),
-                                            c->p.init_field + comp * n, w, w,
-                                            (size_t)g.ny * g.nz, cudaMemcpyDeviceToDevice, s));
+                const int rc = import_dense(c, c->p.init_field, 1, cur, g, 3, s);
+                if (rc != DIR_OK) return rc;
+                if (f64) c->launches += 1;
             } else {
-                CK(c, cudaMemsetAsync(cur, 0, sizeof(float) * 3 * (size_t)g.cs, s));
+                CK(c, cudaMemsetAsync(cur, 0, c->esz * 3 * (size_t)g.cs, s));
             }
         } else {
-            CK(c, dirk::launch_upsample(cur, c->lv[l + 1].g, oth, g, s));
+            CK(c, dirk::launch_upsample(f64, cur, c->lv[l + 1].g, oth, g, s));
             c->launches += 1;
-            float* t = cur;
+            char* t = cur;
             cur = oth;
             oth = t;
         }
@@ -192,53 +237,43 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.S = c->lv[l].S;
         fa.M = c->lv[l].M;
         fa.g = g;
-        fa.zchunk = dirk::force_zchunk(c->variant, g, c->num_sms);
-        fa.alpha2 = c->p.alpha * c->p.alpha;
+        fa.alpha2 = (double)c->p.alpha * (double)c->p.alpha;
         fa.stop_iter = c->ctl + lc;
         dirk::SmoothArgs sa;
         sa.g = g;
         sa.ncomp = 3;
-        sa.zchunk = dirk::smooth_zchunk(g, c->taps.R, c->num_sms);
         sa.taps = c->taps;
         sa.stop_iter = c->ctl + lc;
+        sa.err = c->derr;
         const bool timed = c->p.timing && l == 0;
         for (int it = 0; it < c->p.iters[lc]; ++it, ++row) {
-            if (timed) {
-                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
-                CK(c, capturing ? cudaEventRecordWithFlags(e[0], s, cudaEventRecordExternal)
-                                : cudaEventRecord(e[0], s));
-            }
+            cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
+            if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
             fa.u = cur;
             fa.v = oth;
             fa.red = c->red + 3 * (size_t)row;
             fa.iter = it;
-            CK(c, dirk::launch_force(c->variant, fa, s));
+            CK(c, dirk::launch_force(c->variant, f64, fa, s));
             c->launches += 1;
             if (c->p.stop_mode == 1) {
                 CK(c, dirk::launch_stop_test(c->red, c->lhist, row, c->level_first[lc],
                                              c->p.stop_window, c->p.eps, c->ctl + lc, it, s));
                 c->launches += 1;
             }
-            if (timed) {
-                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
-                CK(c, capturing ? cudaEventRecordWithFlags(e[1], s, cudaEventRecordExternal)
-                                : cudaEventRecord(e[1], s));
-            }
+            if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
             sa.in = oth;
             sa.out = cur;
             sa.iter = it;
-            CK(c, dirk::launch_smooth(sa, s));
+            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
             c->launches += 1;
             if (timed) {
-                cudaEvent_t* e = &c->tev[3 * (size_t)c->n_timed];
-                CK(c, capturing ? cudaEventRecordWithFlags(e[2], s, cudaEventRecordExternal)
-                                : cudaEventRecord(e[2], s));
+                if (record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
                 c->n_timed += 1;
             }
         }
     }
     if (c->variant == DIR_INVERSE_CONSISTENT) {
-        CK(c, dirk::launch_ic_invert(cur, oth, c->lv[0].g, kIcInvertSteps, s));
+        CK(c, dirk::launch_ic_invert(f64, cur, oth, c->lv[0].g, kIcInvertSteps, s));
         c->launches += 1;
         c->final_field = oth;
     } else {
@@ -272,9 +307,10 @@ static int capture_graph(dir_ctx* c) {
 
 static void release(dir_ctx* c) {
     if (!c) return;
-    if (c->stream || c->cap) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     if (c->exec) cudaGraphExecDestroy(c->exec);
-    for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->tev)
+        if (e) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -284,8 +320,10 @@ static void release(dir_ctx* c) {
     cudaFree(c->red);
     cudaFree(c->lhist);
     cudaFree(c->ctl);
+    cudaFree(c->derr);
     cudaFree(c->stage_img);
-    cudaFree(c->stage_dense);
+    cudaFree(c->stage_f32);
+    cudaFree(c->stage_f64);
     delete c;
 }
 
@@ -299,6 +337,7 @@ static int validate_params(const dir_params* p) {
     if (p->stop_mode != 0 && p->stop_mode != 1) return DIR_EINVAL;
     if (p->stop_mode == 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
     if (p->field_dtype != DIR_F32) return DIR_EUNSUPPORTED;
+    if (p->precision != DIR_F32 && p->precision != DIR_F64) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
     return DIR_OK;
 }
@@ -321,6 +360,7 @@ int dir_params_default(dir_params* p) {
     p->init_field = nullptr;
     p->use_graph = 1;
     p->timing = 0;
+    p->precision = DIR_F32;
     return DIR_OK;
 }
 
@@ -374,12 +414,13 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
     }
     c->variant = (int)variant;
     c->p = p;
+    c->fp64 = (p.precision == DIR_F64);
+    c->esz = c->fp64 ? sizeof(double) : sizeof(float);
     c->stream = (cudaStream_t)cuda_stream;
     c->levels = p.levels;
     make_taps(p.sigma, &c->taps);
     make_taps(1.0, &c->taps1);
 
-    int rc = DIR_OK;
     auto fail = [&](int code) {
         if (g_create_error.empty()) g_create_error = c->err;
         release(c);
@@ -406,21 +447,22 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
     c->total_iters = 0;
     for (int l = 0; l < c->levels; ++l) c->total_iters += p.iters[l];
     const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
-    if (cudaMalloc(&c->img_pool, pool * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&c->A, field * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&c->B, field * sizeof(float)) != cudaSuccess ||
+    if (cudaMalloc(&c->img_pool, pool * c->esz) != cudaSuccess ||
+        cudaMalloc(&c->A, field * c->esz) != cudaSuccess ||
+        cudaMalloc(&c->B, field * c->esz) != cudaSuccess ||
         cudaMalloc(&c->red, 3 * nred * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->lhist, nred * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->ctl, DIR_MAX_LEVELS * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&c->ctl, DIR_MAX_LEVELS * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "device allocation failed";
         return fail(DIR_ENOMEM);
     }
     size_t at = 0;
     for (int l = 0; l < c->levels; ++l) {
-        c->lv[l].S = c->img_pool + at;
+        c->lv[l].S = c->img_pool + at * c->esz;
         at += c->lv[l].g.cs;
-        c->lv[l].M = c->img_pool + at;
+        c->lv[l].M = c->img_pool + at * c->esz;
         at += c->lv[l].g.cs;
     }
     e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
@@ -441,12 +483,13 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
             }
         }
     }
-    e = cudaMemsetAsync(c->img_pool, 0, pool * sizeof(float), c->stream);
+    e = cudaMemsetAsync(c->img_pool, 0, pool * c->esz, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) {
         set_err(c, "cudaMemsetAsync", e);
         return fail(DIR_ECUDA);
     }
-    rc = upload_pair(c, static_img, moving_img, inputs_on_device, c->stream);
+    const int rc = upload_pair(c, static_img, moving_img, inputs_on_device, c->stream);
     if (rc != DIR_OK) return fail(rc);
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -494,12 +537,18 @@ int dir_sync(dir_ctx* c, dir_stats* st) {
     c->pending = false;
     const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
     c->red_host.resize(3 * nred);
-    c->ctl_host.resize(DIR_MAX_LEVELS);
+    c->ctl_host.resize(DIR_MAX_LEVELS + 1);
     CK(c, cudaMemcpyAsync(c->red_host.data(), c->red, 3 * nred * sizeof(double),
                           cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(c->ctl_host.data(), c->ctl, c->levels * sizeof(int),
                           cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(c->ctl_host.data() + DIR_MAX_LEVELS, c->derr, sizeof(int),
+                          cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (c->ctl_host[DIR_MAX_LEVELS] != 0) {
+        c->err = "a device-side wait for a tensor copy timed out";
+        return DIR_ETIMEOUT;
+    }
     c->have_field = true;
     long long vu = 0;
     for (int lc = 0; lc < c->levels; ++lc) {
@@ -569,28 +618,36 @@ int dir_get_history(dir_ctx* c, double* out, int max_iters) {
     return w;
 }
 
-int dir_get_field(dir_ctx* c, float* out, int in_mm, int out_on_device) {
+static int get_field(dir_ctx* c, void* out, int in_mm, int out_on_device, bool out_fp64) {
     if (!c || !out) return DIR_EINVAL;
     if (!c->have_field || !c->final_field) return DIR_ESTATE;
     const Grid3& g = c->lv[0].g;
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
-    float* dst = out;
+    const size_t n = c->nvox();
+    const size_t osz = out_fp64 ? sizeof(double) : sizeof(float);
+    void* dst = out;
     if (!out_on_device) {
-        if (!c->stage_dense && cudaMalloc(&c->stage_dense, 3 * n * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            c->stage_dense = nullptr;
-            return DIR_ENOMEM;
-        }
-        dst = c->stage_dense;
+        void** stage = out_fp64 ? (void**)&c->stage_f64 : (void**)&c->stage_f32;
+        const int rc = ensure(c, stage, 3 * n * osz);
+        if (rc != DIR_OK) return rc;
+        dst = *stage;
     }
-    const float sx = in_mm ? c->spacing[0] : 1.0f;
-    const float sy = in_mm ? c->spacing[1] : 1.0f;
-    const float sz = in_mm ? c->spacing[2] : 1.0f;
-    CK(c, dirk::launch_export_field(c->final_field, g, sx, sy, sz, dst, c->stream));
+    const double sx = in_mm ? c->spacing[0] : 1.0;
+    const double sy = in_mm ? c->spacing[1] : 1.0;
+    const double sz = in_mm ? c->spacing[2] : 1.0;
+    CK(c, dirk::launch_export_field(c->fp64, c->final_field, g, sx, sy, sz, dst, out_fp64,
+                                    c->stream));
     if (!out_on_device)
-        CK(c, cudaMemcpyAsync(out, dst, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(out, dst, 3 * n * osz, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return DIR_OK;
+}
+
+int dir_get_field(dir_ctx* c, float* out, int in_mm, int out_on_device) {
+    return get_field(c, out, in_mm, out_on_device, false);
+}
+
+int dir_get_field_f64(dir_ctx* c, double* out, int in_mm, int out_on_device) {
+    return get_field(c, out, in_mm, out_on_device, true);
 }
 
 int dir_warp(dir_ctx* c, const void* img_in, void* img_out, dir_dtype dt, int on_device) {
@@ -598,27 +655,18 @@ int dir_warp(dir_ctx* c, const void* img_in, void* img_out, dir_dtype dt, int on
     if (dt != DIR_F32) return DIR_EUNSUPPORTED;
     if (!c->have_field || !c->final_field) return DIR_ESTATE;
     const Grid3& g = c->lv[0].g;
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
-    if (!c->stage_img && cudaMalloc(&c->stage_img, (size_t)g.cs * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        c->stage_img = nullptr;
-        return DIR_ENOMEM;
-    }
-    const size_t w = (size_t)g.nx * sizeof(float);
-    CK(c, cudaMemcpy2DAsync(c->stage_img, (size_t)g.px * sizeof(float), img_in, w, w,
-                            (size_t)g.ny * g.nz,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            c->stream));
+    const size_t n = c->nvox();
+    int rc = ensure(c, (void**)&c->stage_img, (size_t)g.cs * c->esz);
+    if (rc != DIR_OK) return rc;
+    rc = import_dense(c, (const float*)img_in, on_device, c->stage_img, g, 1, c->stream);
+    if (rc != DIR_OK) return rc;
     float* dst = (float*)img_out;
     if (!on_device) {
-        if (!c->stage_dense && cudaMalloc(&c->stage_dense, 3 * n * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            c->stage_dense = nullptr;
-            return DIR_ENOMEM;
-        }
-        dst = c->stage_dense;
+        rc = ensure(c, (void**)&c->stage_f32, 3 * n * sizeof(float));
+        if (rc != DIR_OK) return rc;
+        dst = c->stage_f32;
     }
-    CK(c, dirk::launch_warp(c->stage_img, c->final_field, g, dst, c->stream));
+    CK(c, dirk::launch_warp(c->fp64, c->stage_img, c->final_field, g, dst, c->stream));
     if (!on_device)
         CK(c, cudaMemcpyAsync(img_out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -635,12 +683,13 @@ const char* dir_status_string(int s) {
         case DIR_ECUDA: return "CUDA error";
         case DIR_ESTATE: return "call out of order";
         case DIR_EUNSUPPORTED: return "not supported by this build";
+        case DIR_ETIMEOUT: return "device-side wait timed out";
         default: return "unknown status";
     }
 }
 
 const char* dir_last_error(const dir_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
-const char* dir_version(void) { return "gb300-demons 0.1 (sm_103a)"; }
+const char* dir_version(void) { return "gb300-demons 0.2 (sm_103a)"; }
 
 }  // extern "C"

@@ -1,7 +1,7 @@
 // dir_misc.cu -- once-per-level and once-per-registration kernels:
 // pyramid decimation and field up-sampling (Sec. 2.3), the final warp
 // (Sec. 2.5 interpolation), the inverse-consistent output field (Eq. 6), field
-// export, and the relative-norm stop test (Sec. 2.4).
+// import/export, and the relative-norm stop test (Sec. 2.4).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -16,7 +16,8 @@ static dim3 grid_for(const Grid3& g) {
     return dim3((g.nx + MTX - 1) / MTX, (g.ny + MTY - 1) / MTY, g.nz);
 }
 
-__global__ void decimate_kernel(const float* __restrict__ in, Grid3 gi, float* __restrict__ out,
+template <typename Real>
+__global__ void decimate_kernel(const Real* __restrict__ in, Grid3 gi, Real* __restrict__ out,
                                 Grid3 go) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
@@ -24,62 +25,79 @@ __global__ void decimate_kernel(const float* __restrict__ in, Grid3 gi, float* _
     out[offs(go, x, y, z)] = __ldg(in + offs(gi, 2 * x, 2 * y, 2 * z));
 }
 
-__global__ void upsample_kernel(const float* __restrict__ coarse, Grid3 gc,
-                                float* __restrict__ fine, Grid3 gf) {
+template <typename Real>
+__global__ void upsample_kernel(const Real* __restrict__ coarse, Grid3 gc, Real* __restrict__ fine,
+                                Grid3 gf) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= gf.nx || y >= gf.ny) return;
-    const float cx = 0.5f * x, cy = 0.5f * y, cz = 0.5f * z;
+    const Real cx = Real(0.5) * x, cy = Real(0.5) * y, cz = Real(0.5) * z;
     const long long o = offs(gf, x, y, z);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) fine[o + c * gf.cs] = 2.0f * trilinear(coarse + c * gc.cs, gc, cx, cy, cz);
+    for (int c = 0; c < 3; ++c)
+        fine[o + c * gf.cs] = Real(2) * trilinear(coarse + c * gc.cs, gc, cx, cy, cz);
 }
 
-__global__ void warp_kernel(const float* __restrict__ img, const float* __restrict__ u, Grid3 g,
+template <typename Real>
+__global__ void warp_kernel(const Real* __restrict__ img, const Real* __restrict__ u, Grid3 g,
                             float* __restrict__ out) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long o = offs(g, x, y, z);
-    const float w = trilinear(img, g, x + __ldg(u + o), y + __ldg(u + o + g.cs),
-                              z + __ldg(u + o + 2 * g.cs));
-    out[(long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z)] = w;
+    const Real w = trilinear(img, g, (Real)x + __ldg(u + o), (Real)y + __ldg(u + o + g.cs),
+                             (Real)z + __ldg(u + o + 2 * g.cs));
+    out[(long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z)] = (float)w;
 }
 
-__global__ void ic_invert_kernel(const float* __restrict__ h, float* __restrict__ u, Grid3 g,
+template <typename Real>
+__global__ void ic_invert_kernel(const Real* __restrict__ h, Real* __restrict__ u, Grid3 g,
                                  int steps) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const float* hx = h;
-    const float* hy = h + g.cs;
-    const float* hz = h + 2 * g.cs;
-    float px = (float)x, py = (float)y, pz = (float)z;
+    const Real* hx = h;
+    const Real* hy = h + g.cs;
+    const Real* hz = h + 2 * g.cs;
+    Real px = (Real)x, py = (Real)y, pz = (Real)z;
     for (int s = 0; s < steps; ++s) {
-        const float ax = trilinear(hx, g, px, py, pz);
-        const float ay = trilinear(hy, g, px, py, pz);
-        const float az = trilinear(hz, g, px, py, pz);
-        px = x + ax;
-        py = y + ay;
-        pz = z + az;
+        const Real ax = trilinear(hx, g, px, py, pz);
+        const Real ay = trilinear(hy, g, px, py, pz);
+        const Real az = trilinear(hz, g, px, py, pz);
+        px = (Real)x + ax;
+        py = (Real)y + ay;
+        pz = (Real)z + az;
     }
     const long long o = offs(g, x, y, z);
-    u[o] = 2.0f * trilinear(hx, g, px, py, pz);
-    u[o + g.cs] = 2.0f * trilinear(hy, g, px, py, pz);
-    u[o + 2 * g.cs] = 2.0f * trilinear(hz, g, px, py, pz);
+    u[o] = Real(2) * trilinear(hx, g, px, py, pz);
+    u[o + g.cs] = Real(2) * trilinear(hy, g, px, py, pz);
+    u[o + 2 * g.cs] = Real(2) * trilinear(hz, g, px, py, pz);
 }
 
-__global__ void export_kernel(const float* __restrict__ f, Grid3 g, float sx, float sy, float sz,
-                              float* __restrict__ dense) {
+template <typename Real, typename Out>
+__global__ void export_kernel(const Real* __restrict__ f, Grid3 g, double sx, double sy, double sz,
+                              Out* __restrict__ dense) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long n = (long long)g.nx * g.ny * g.nz;
     const long long o = offs(g, x, y, z);
     const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-    dense[d] = sx * f[o];
-    dense[d + n] = sy * f[o + g.cs];
-    dense[d + 2 * n] = sz * f[o + 2 * g.cs];
+    dense[d] = (Out)((Real)sx * f[o]);
+    dense[d + n] = (Out)((Real)sy * f[o + g.cs]);
+    dense[d + 2 * n] = (Out)((Real)sz * f[o + 2 * g.cs]);
+}
+
+template <typename Real>
+__global__ void import_kernel(const float* __restrict__ dense, Real* __restrict__ f, Grid3 g,
+                              int ncomp) {
+    const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    const long long o = offs(g, x, y, z);
+    const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    for (int c = 0; c < ncomp; ++c) f[o + c * g.cs] = (Real)dense[d + c * n];
 }
 
 // Sec. 2.4: l(t) = sum|du| / sum|u|; stop the level after iteration t when
@@ -97,32 +115,64 @@ __global__ void stop_test_kernel(const double* __restrict__ red, double* lhist, 
     }
 }
 
-cudaError_t launch_decimate(const float* in, const Grid3& gin, float* out, const Grid3& gout,
-                            cudaStream_t s) {
-    decimate_kernel<<<grid_for(gout), dim3(MTX, MTY), 0, s>>>(in, gin, out, gout);
+#define DIR_DISPATCH(fp64, CALL)          \
+    do {                                  \
+        if (fp64) {                       \
+            using Real = double;          \
+            CALL;                         \
+        } else {                          \
+            using Real = float;           \
+            CALL;                         \
+        }                                 \
+    } while (0)
+
+cudaError_t launch_decimate(bool fp64, const void* in, const Grid3& gin, void* out,
+                            const Grid3& gout, cudaStream_t s) {
+    DIR_DISPATCH(fp64, (decimate_kernel<Real><<<grid_for(gout), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const Real*>(in), gin, static_cast<Real*>(out), gout)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_upsample(const float* coarse, const Grid3& gc, float* fine, const Grid3& gf,
-                            cudaStream_t s) {
-    upsample_kernel<<<grid_for(gf), dim3(MTX, MTY), 0, s>>>(coarse, gc, fine, gf);
+cudaError_t launch_upsample(bool fp64, const void* coarse, const Grid3& gc, void* fine,
+                            const Grid3& gf, cudaStream_t s) {
+    DIR_DISPATCH(fp64, (upsample_kernel<Real><<<grid_for(gf), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const Real*>(coarse), gc, static_cast<Real*>(fine), gf)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp(const float* img, const float* u, const Grid3& g, float* out_dense,
-                        cudaStream_t s) {
-    warp_kernel<<<grid_for(g), dim3(MTX, MTY), 0, s>>>(img, u, g, out_dense);
+cudaError_t launch_warp(bool fp64, const void* img, const void* u, const Grid3& g,
+                        float* out_dense, cudaStream_t s) {
+    DIR_DISPATCH(fp64, (warp_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const Real*>(img), static_cast<const Real*>(u), g,
+                           out_dense)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_ic_invert(const float* h, float* u, const Grid3& g, int steps, cudaStream_t s) {
-    ic_invert_kernel<<<grid_for(g), dim3(MTX, MTY), 0, s>>>(h, u, g, steps);
+cudaError_t launch_ic_invert(bool fp64, const void* h, void* u, const Grid3& g, int steps,
+                             cudaStream_t s) {
+    DIR_DISPATCH(fp64, (ic_invert_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const Real*>(h), static_cast<Real*>(u), g, steps)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_field(const float* field, const Grid3& g, float sx, float sy, float sz,
-                                float* dense, cudaStream_t s) {
-    export_kernel<<<grid_for(g), dim3(MTX, MTY), 0, s>>>(field, g, sx, sy, sz, dense);
+cudaError_t launch_export_field(bool fp64, const void* field, const Grid3& g, double sx,
+                                double sy, double sz, void* dense, bool out_fp64, cudaStream_t s) {
+    if (out_fp64) {
+        DIR_DISPATCH(fp64, (export_kernel<Real, double><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                               static_cast<const Real*>(field), g, sx, sy, sz,
+                               static_cast<double*>(dense))));
+    } else {
+        DIR_DISPATCH(fp64, (export_kernel<Real, float><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                               static_cast<const Real*>(field), g, sx, sy, sz,
+                               static_cast<float*>(dense))));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import(bool fp64, const float* dense, void* pitched, const Grid3& g, int ncomp,
+                          cudaStream_t s) {
+    DIR_DISPATCH(fp64, (import_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                           dense, static_cast<Real*>(pitched), g, ncomp)));
     return cudaGetLastError();
 }
 

@@ -3,10 +3,18 @@
 // out = G_sigma * in, applied along x, then y, then z, with replicated edges,
 // on 1 or 3 components.  The paper stages data in shared memory so that the
 // strided y and z passes stay coalesced; here a block owns a 32 x 8 column tile
-// and marches through a chunk of z planes: each input plane (tile plus an R
-// halo in x and y) is staged in shared memory, the x and y passes run there,
-// and the z pass is a rolling window of 2R+1 y-filtered planes held in
-// registers, so every input voxel is read from HBM about once.
+// and marches through a chunk of z planes:
+//   * one thread issues TMA tensor copies (cp.async.bulk.tensor) of each input
+//     plane's tile plus halo, all components at once, into a 4-slot ring of
+//     shared memory, several planes ahead, each slot completing on its own
+//     mbarrier;
+//   * edge tiles overwrite the zero-filled out-of-volume cells with the nearest
+//     edge voxel (replicate boundary) in shared memory;
+//   * the x and y passes run in shared memory; the z pass is a rolling window
+//     of 2R+1 y-filtered planes held in registers.
+// Every input voxel is read from HBM about once per launch (plus the 2R-plane
+// halo of each z chunk).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "dir_common.cuh"
@@ -14,72 +22,136 @@
 
 namespace dirk {
 
-constexpr int STX = 32, STY = 8, SNT = STX * STY;
+constexpr int STX = 32, STY = 8, SNT = STX * STY, STAGES = 4;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-template <int R, int NC>
-__global__ void __launch_bounds__(SNT) smooth_kernel(const SmoothArgs a) {
+template <typename Real, int R, int NC>
+struct SmoothGeom {
+    static constexpr int HA = (R + 3) / 4 * 4;   // x halo rounded up: TMA x start 16-byte aligned
+    static constexpr int WB = STX + 2 * HA;      // box width
+    static constexpr int H = STY + 2 * R;        // box height
+    static constexpr int K = 2 * R + 1;
+    static constexpr int SLOT_ELEMS = NC * H * WB;
+    static constexpr int SLOT_BYTES = SLOT_ELEMS * (int)sizeof(Real);
+    static constexpr int SLOT_STRIDE = (SLOT_BYTES + 127) / 128 * 128;
+    static constexpr int TXP_BYTES = NC * H * STX * (int)sizeof(Real);
+    static constexpr int SMEM = 128 /*align slack*/ + STAGES * SLOT_STRIDE + TXP_BYTES + 64;
+};
+
+template <typename Real, int R, int NC>
+__global__ void __launch_bounds__(SNT) smooth_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                     const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
-    constexpr int W = STX + 2 * R, H = STY + 2 * R, K = 2 * R + 1;
-    __shared__ float tin[NC][H][W];
-    __shared__ float txp[NC][H][STX];
+    using G = SmoothGeom<Real, R, NC>;
+    constexpr int HA = G::HA, WB = G::WB, H = G::H, K = G::K;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    Real* txp = reinterpret_cast<Real*>(base + STAGES * G::SLOT_STRIDE);          // [NC][H][STX]
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * G::SLOT_STRIDE + G::TXP_BYTES);
+
     const Grid3 g = a.g;
-    const float* __restrict__ in = a.in;
-    float* __restrict__ out = a.out;
-    float w[K];
+    Real* __restrict__ out = static_cast<Real*>(a.out);
+    Real w[K];
 #pragma unroll
-    for (int t = 0; t < K; ++t) w[t] = a.taps.w[t];
+    for (int t = 0; t < K; ++t) w[t] = (Real)a.taps.w[t];
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + STX * ty;
     const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;
     const int x = x0 + tx, y = y0 + ty;
     const bool valid = (x < g.nx) && (y < g.ny);
-    const int z0 = blockIdx.z * a.zchunk;
-    const int z1 = min(z0 + a.zchunk, g.nz);
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const int nsteps = (z1 - z0) + 2 * R;  // input planes z0-R .. z1-1+R (clamped)
+    const int bx = x0 - HA, by = y0 - R;   // box origin in the volume
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
 
-    float ring[K][NC];
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+        fence_proxy_async();
+    }
+    __syncthreads();
+    auto issue = [&](int step) {
+        const int s = step % STAGES;
+        const int pc = clampi(z0 - R + step, 0, g.nz - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[s], (uint32_t)G::SLOT_BYTES);
+        tma_load_4d(base + s * G::SLOT_STRIDE, &tmap, bx, by, pc, 0, &full[s]);
+    };
+    if (tid == 0) {
+        for (int st = 0; st < STAGES - 1 && st < nsteps; ++st) issue(st);
+    }
+
+    Real ring[K][NC];
 #pragma unroll
     for (int t = 0; t < K; ++t)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) ring[t][c] = 0.0f;
+        for (int c = 0; c < NC; ++c) ring[t][c] = Real(0);
 
-    for (int p = z0 - R; p < z1 + R; ++p) {
-        const int pc = clampi(p, 0, g.nz - 1);
-        for (int q = tid; q < W * H; q += SNT) {
-            const int hy = q / W, hx = q - hy * W;
-            const int gx = clampi(x0 + hx - R, 0, g.nx - 1);
-            const int gy = clampi(y0 + hy - R, 0, g.ny - 1);
-            const long long o = offs(g, gx, gy, pc);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) tin[c][hy][hx] = __ldg(in + o + c * g.cs);
+    for (int step = 0; step < nsteps; ++step) {
+        // refill the slot freed by the previous step (all threads are past its reads)
+        if (tid == 0 && step + STAGES - 1 < nsteps) issue(step + STAGES - 1);
+        const int s = step % STAGES;
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((step / STAGES) & 1), kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+            return;
+        }
+        Real* slot = reinterpret_cast<Real*>(base + s * G::SLOT_STRIDE);  // [NC][H][WB]
+        if (edge) {
+            // replicate boundary: columns first (within every row), then rows
+            for (int q = tid; q < NC * H * WB; q += SNT) {
+                const int hx = q % WB;
+                const int gx = bx + hx;
+                if (gx < 0 || gx >= g.nx) {
+                    const int src = clampi(gx, 0, g.nx - 1) - bx;  // in-volume column
+                    slot[q] = slot[q - hx + src];
+                }
+            }
+            __syncthreads();
+            for (int q = tid; q < NC * H * WB; q += SNT) {
+                const int hx = q % WB;
+                const int r = q / WB;
+                const int hy = r % H;
+                const int gy = by + hy;
+                if (gy < 0 || gy >= g.ny) {
+                    const int src = clampi(gy, 0, g.ny - 1) - by;
+                    slot[q] = slot[(r - hy + src) * WB + hx];
+                }
+            }
         }
         __syncthreads();
+        // x pass: rows of the tile plus the y halo
         for (int q = tid; q < STX * H; q += SNT) {
             const int r = q / STX, cc = q - r * STX;
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                float acc = 0.0f;
+                const Real* row = slot + (c * H + r) * WB + (HA - R) + cc;
+                Real acc = Real(0);
 #pragma unroll
-                for (int t = 0; t < K; ++t) acc += w[t] * tin[c][r][cc + t];
-                txp[c][r][cc] = acc;
+                for (int t = 0; t < K; ++t) acc += w[t] * row[t];
+                txp[(c * H + r) * STX + cc] = acc;
             }
         }
         __syncthreads();
+        // y pass into the register ring, then the z pass
 #pragma unroll
         for (int t = 0; t < K - 1; ++t)
 #pragma unroll
             for (int c = 0; c < NC; ++c) ring[t][c] = ring[t + 1][c];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            float acc = 0.0f;
+            Real acc = Real(0);
 #pragma unroll
-            for (int t = 0; t < K; ++t) acc += w[t] * txp[c][ty + t][tx];
+            for (int t = 0; t < K; ++t) acc += w[t] * txp[(c * H + ty + t) * STX + tx];
             ring[K - 1][c] = acc;
         }
-        if (p >= z0 + R && valid) {
-            const long long o = offs(g, x, y, p - R);
+        if (step >= 2 * R && valid) {
+            const long long o = offs(g, x, y, z0 + step - 2 * R);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                float acc = 0.0f;
+                Real acc = Real(0);
 #pragma unroll
                 for (int t = 0; t < K; ++t) acc += w[t] * ring[t][c];
                 out[o + c * g.cs] = acc;
@@ -88,43 +160,94 @@ __global__ void __launch_bounds__(SNT) smooth_kernel(const SmoothArgs a) {
     }
 }
 
-int smooth_zchunk(const Grid3& g, int radius, int num_sms) {
-    const long long bxy = (long long)((g.nx + STX - 1) / STX) * ((g.ny + STY - 1) / STY);
-    const long long target = 4LL * num_sms;
-    long long chunks = (target + bxy - 1) / bxy;
-    if (chunks < 1) chunks = 1;
-    int zc = (int)((g.nz + chunks - 1) / chunks);
-    const int zmin = 4 * radius;  // keep the 2R-plane halo small against the chunk
-    if (zc < zmin) zc = zmin;
-    if (zc > g.nz) zc = g.nz;
-    return zc < 1 ? 1 : zc;
+// ---------------------------------------------------------------- host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
 }
 
-template <int R>
-static cudaError_t launch_r(const SmoothArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
-    if (a.ncomp == 3)
-        smooth_kernel<R, 3><<<grid, block, 0, s>>>(a);
-    else
-        smooth_kernel<R, 1><<<grid, block, 0, s>>>(a);
+template <typename Real, int R, int NC>
+static cudaError_t launch_rn(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    using G = SmoothGeom<Real, R, NC>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // 4-D view: (x, y, z, component), strides in bytes
+    const cuuint64_t dims[4] = {(cuuint64_t)a.g.nx, (cuuint64_t)a.g.ny, (cuuint64_t)a.g.nz,
+                                (cuuint64_t)NC};
+    const cuuint64_t strides[3] = {(cuuint64_t)a.g.px * sizeof(Real),
+                                   (cuuint64_t)a.g.plane * sizeof(Real),
+                                   (cuuint64_t)a.g.cs * sizeof(Real)};
+    const cuuint32_t box[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, 1u, (cuuint32_t)NC};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUtensorMap map;
+    const CUresult r = enc(&map, sizeof(Real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           4, const_cast<void*>(a.in), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(smooth_kernel<Real, R, NC>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    // z chunk: about one wave of resident blocks, each chunk at least 4R planes
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R, NC>, SNT,
+                                                  G::SMEM);
+    if (per_sm < 1) per_sm = 1;
+    const long long bxy = (long long)((a.g.nx + STX - 1) / STX) * ((a.g.ny + STY - 1) / STY);
+    const long long target = (long long)per_sm * num_sms;
+    long long chunks = (target + bxy - 1) / bxy;
+    if (chunks < 1) chunks = 1;
+    int zc = (int)((a.g.nz + chunks - 1) / chunks);
+    if (zc < 4 * R) zc = 4 * R;
+    if (zc > a.g.nz) zc = a.g.nz;
+    const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY, (a.g.nz + zc - 1) / zc);
+    smooth_kernel<Real, R, NC><<<grid, dim3(STX, STY, 1), G::SMEM, s>>>(map, a, zc);
     return cudaGetLastError();
 }
 
-cudaError_t launch_smooth(const SmoothArgs& a, cudaStream_t s) {
-    if (a.ncomp != 1 && a.ncomp != 3) return cudaErrorInvalidValue;
-    const dim3 block(STX, STY, 1);
-    const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY,
-                    (a.g.nz + a.zchunk - 1) / a.zchunk);
+template <typename Real, int R>
+static cudaError_t launch_r(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    return a.ncomp == 3 ? launch_rn<Real, R, 3>(a, num_sms, s) : launch_rn<Real, R, 1>(a, num_sms, s);
+}
+
+template <typename Real>
+static cudaError_t launch_t(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     switch (a.taps.R) {
-        case 1: return launch_r<1>(a, grid, block, s);
-        case 2: return launch_r<2>(a, grid, block, s);
-        case 3: return launch_r<3>(a, grid, block, s);
-        case 4: return launch_r<4>(a, grid, block, s);
-        case 5: return launch_r<5>(a, grid, block, s);
-        case 6: return launch_r<6>(a, grid, block, s);
-        case 7: return launch_r<7>(a, grid, block, s);
-        case 8: return launch_r<8>(a, grid, block, s);
+        case 1: return launch_r<Real, 1>(a, num_sms, s);
+        case 2: return launch_r<Real, 2>(a, num_sms, s);
+        case 3: return launch_r<Real, 3>(a, num_sms, s);
+        case 4: return launch_r<Real, 4>(a, num_sms, s);
+        case 5: return launch_r<Real, 5>(a, num_sms, s);
+        case 6: return launch_r<Real, 6>(a, num_sms, s);
+        case 7: return launch_r<Real, 7>(a, num_sms, s);
+        case 8: return launch_r<Real, 8>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    if (a.ncomp != 1 && a.ncomp != 3) return cudaErrorInvalidValue;
+    return fp64 ? launch_t<double>(a, num_sms, s) : launch_t<float>(a, num_sms, s);
 }
 
 }  // namespace dirk
