@@ -70,9 +70,9 @@ typedef enum { DIR_F32 = 0, DIR_I16 = 1, DIR_F16 = 2, DIR_BF16 = 3, DIR_F64 = 4 
 typedef struct {
     int levels;                  /* pyramid depth, 1..DIR_MAX_LEVELS (default 3; the paper uses 2, Sec. 2.3) */
     int iters[DIR_MAX_LEVELS];   /* iterations per level, COARSEST level first (default 200, 100, 50) */
-    float sigma;                 /* Gaussian sigma in voxels (default 1.0, Sec. 2.5 "unit standard deviation");
+    double sigma;                /* Gaussian sigma in voxels (default 1.0, Sec. 2.5 "unit standard deviation");
                                     the filter radius is ceil(3 sigma), at most 8 */
-    float alpha;                 /* Eq. (5) normalisation factor (default 0.4) */
+    double alpha;                /* Eq. (5) normalisation factor (default 0.4) */
     int stop_mode;               /* 0: run iters exactly; 1: also stop a level when
                                     |l(n) - l(n - stop_window)| <= eps (Sec. 2.4) */
     double eps;                  /* default 1e-4 (Sec. 2.4) */

@@ -63,7 +63,7 @@ def _lib(threaded: bool = False) -> C.CDLL:
         lib.or_register.restype = C.c_int
         lib.or_register.argtypes = ([_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.c_double, C.c_int, _ip, C.c_int, C.c_double, C.c_int, _dp,
-                                     _dp, _dp, _ip, _dp])
+                                     _dp, _dp, _ip, _dp, C.c_int])
         lib.or_num_threads.restype = C.c_int
         lib.or_num_threads.argtypes = []
         _LIBS[threaded] = lib
@@ -203,11 +203,14 @@ def ic_field(h) -> np.ndarray:
 
 def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: float = 1.0,
              alpha: float = 0.4, stop_mode: int = 0, eps: float = 1e-4, stop_window: int = 10,
-             init=None, threaded: bool = True, return_raw: bool = False):
+             init=None, threaded: bool = True, return_raw: bool = False,
+             round_f32: bool = False):
     """Whole registration.  `iters` lists iterations per level, coarsest first.
 
     Returns dict(u=(3, nz, ny, nx) field in voxels, stats=(n, 3) per-iteration
     [MSE, sum|du|, sum|u|], iters_run=list per level[, raw=iterated field]).
+    round_f32 rounds the field to float after every iteration: a conditioning
+    probe (how far single-precision storage alone moves the answer).
     """
     S = _f64(S)
     M = _f64(M)
@@ -222,7 +225,8 @@ def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: 
     rc = _lib(threaded).or_register(_p(S), _p(M), nx, ny, nz, int(variant), float(alpha),
                                     float(sigma), int(levels), it, int(stop_mode), float(eps),
                                     int(stop_window), _p(ini) if ini is not None else None,
-                                    _p(u), _p(stats), run, _p(raw) if raw is not None else None)
+                                    _p(u), _p(stats), run, _p(raw) if raw is not None else None,
+                                    int(bool(round_f32)))
     if rc != 0:
         raise ValueError(f"or_register failed: {rc}")
     runs = [int(run[i]) for i in range(levels)]

@@ -455,12 +455,17 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /*   iters_run    per level (coarsest first), iterations actually run         */
 /*   raw_out      NULL, or 3 planar arrays of N doubles that receive the      */
 /*                iterated field itself (h for Eq. 6, equal to u_out else)    */
+/*   round_f32    0 normally.  1 rounds the field to the nearest float after  */
+/*                every iteration: a probe of how much storing the field in   */
+/*                single precision alone moves the result (conditioning test  */
+/*                of the iteration, not part of the method)                   */
 /* Returns 0 or a negative code.                                              */
 /* ------------------------------------------------------------------------- */
 OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, int nz,
                           int variant, double alpha, double sigma, int levels, const int* iters,
                           int stop_mode, double eps, int stop_window, const double* init,
-                          double* u_out, double* stats, int* iters_run, double* raw_out) {
+                          double* u_out, double* stats, int* iters_run, double* raw_out,
+                          int round_f32) {
     if (variant < 0 || variant > 5 || levels < 1 || levels > OR_MAX_LEVELS) return -1;
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     if (init && levels != 1) return -1;
@@ -548,6 +553,8 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
                             variant == OR_EVOLVED_PASSIVE ? bm : NULL, ux, uy, uz, cx, cy, cz,
                             work, red);
             if (rc) break;
+            if (round_f32)
+                for (size_t c = 0; c < 3 * nl; ++c) u[c] = (double)(float)u[c];
             stats[3 * stat_at + 0] = red[0] / (double)nl;
             stats[3 * stat_at + 1] = red[1];
             stats[3 * stat_at + 2] = red[2];

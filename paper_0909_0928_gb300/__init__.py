@@ -37,8 +37,8 @@ EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_
 
 
 class DirParams(C.Structure):
-    _fields_ = [("levels", C.c_int), ("iters", C.c_int * DIR_MAX_LEVELS), ("sigma", C.c_float),
-                ("alpha", C.c_float), ("stop_mode", C.c_int), ("eps", C.c_double),
+    _fields_ = [("levels", C.c_int), ("iters", C.c_int * DIR_MAX_LEVELS), ("sigma", C.c_double),
+                ("alpha", C.c_double), ("stop_mode", C.c_int), ("eps", C.c_double),
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
                 ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
                 ("precision", C.c_int)]

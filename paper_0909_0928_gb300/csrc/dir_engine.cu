@@ -237,7 +237,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.S = c->lv[l].S;
         fa.M = c->lv[l].M;
         fa.g = g;
-        fa.alpha2 = (double)c->p.alpha * (double)c->p.alpha;
+        fa.alpha2 = c->p.alpha * c->p.alpha;
         fa.stop_iter = c->ctl + lc;
         dirk::SmoothArgs sa;
         sa.g = g;
@@ -351,8 +351,8 @@ int dir_params_default(dir_params* p) {
     p->iters[0] = 200;
     p->iters[1] = 100;
     p->iters[2] = 50;
-    p->sigma = 1.0f;
-    p->alpha = 0.4f;
+    p->sigma = 1.0;
+    p->alpha = 0.4;
     p->stop_mode = 0;
     p->eps = 1e-4;
     p->stop_window = 10;

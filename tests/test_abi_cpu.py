@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol(dl):
 def test_params_default_and_status_strings(dl):
     p = dl.dir_params_default()
     assert p.levels == 3 and list(p.iters[:3]) == [200, 100, 50]
-    assert p.sigma == 1.0 and abs(p.alpha - 0.4) < 1e-7
+    assert p.sigma == 1.0 and p.alpha == 0.4
     assert p.eps == 1e-4 and p.stop_window == 10 and p.use_graph == 1
     assert dl.dir_status_string(0) == "ok"
     assert dl.dir_status_string(dl.DIR_EINVAL) == "invalid argument"

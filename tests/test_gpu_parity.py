@@ -6,14 +6,15 @@ Two precisions of the same kernels are checked:
   FP64 oracle to TOL_U64 everywhere, for every variant and size, including the
   ill-conditioned ones.  This checks the arithmetic itself.
 * DIR_F32 (production): max |du| <= 1e-3 voxel and relative RMS <= 1e-4 of the
-  warped image, on every voxel where the problem is conditioned for FP32
-  arithmetic.  The conditioning is measured with the oracle alone: each input
-  voxel is perturbed by one FP32 ulp (relative 2^-23) and the oracle rerun; a
-  voxel whose oracle answer moves by more than COND voxel cannot be computed to
-  the 1e-3 bar by any FP32 implementation (the iteration amplifies rounding
-  there, mostly on clamped boundary planes and for the double/adjusted forces).
-  Such voxels are reported and excluded from the strict bar, and they may
-  never cover more than MAX_ILL of the volume.
+  warped image.  Whether a case is conditioned for FP32 arithmetic is measured
+  with the oracle alone: a probe reruns it with its field rounded to float
+  after every iteration.  Where that probe moves the answer by more than COND
+  voxel, no FP32 implementation can promise the 1e-3 bar (the iteration
+  amplifies rounding there: the double and adjusted forces, whose steps reach
+  1 and 1/alpha voxel, on clamped boundary planes).  A case whose probe stays
+  within COND everywhere is "certified" and held to the bar on every voxel; on
+  other cases the bar applies to the voxels where the probe stays within
+  COND_MASK, which must cover at least 1 - MAX_ILL of the volume.
 
 Sizes run from tiny degenerate volumes through ragged multi-tile ones to the
 full 256 x 256 x 100 workload in the same launch configuration the benchmark
@@ -29,8 +30,9 @@ pytestmark = pytest.mark.gpu
 TOL_U = 1e-3      # voxel, FP32 path
 TOL_W = 1e-4      # relative RMS of the warped image, FP32 path
 TOL_U64 = 1e-6    # voxel, FP64 path
-COND = 1e-4       # oracle sensitivity (voxel) to a one-ulp FP32 input perturbation
-MAX_ILL = 0.6     # largest excluded fraction of voxels
+COND = 1e-4       # probe bound (voxel) that certifies a case for FP32
+COND_MASK = 1e-5  # probe bound for a voxel to count in an uncertified case
+MAX_ILL = 0.05    # largest excluded fraction of voxels
 
 
 @pytest.fixture(scope="module")
@@ -65,31 +67,29 @@ def gpu_register(dl, S, M, variant, levels, iters, alpha=0.4, sigma=1.0, spacing
     return {"u": u, "hist": hist, "stats": st.as_dict(), "W": W}
 
 
-def ulp_sensitivity(S, M, variant, levels, iters, alpha=0.4, sigma=1.0, ref=None, samples=1,
-                    seed=0):
-    """Per-voxel max |u_oracle(perturbed) - u_oracle|, inputs perturbed by one
-    FP32 ulp (relative 2^-23, random sign or zero per voxel)."""
+def fp32_probe(S, M, variant, levels, iters, alpha=0.4, sigma=1.0, ref=None):
+    """Per-voxel |u(oracle with its field rounded to float every iteration) -
+    u(oracle)|: how far single-precision storage alone moves the answer."""
     import oracle
-    from phantom import SplitMix64Stream
     if ref is None:
         ref = oracle.register(S, M, variant=variant, levels=levels, iters=iters, alpha=alpha,
                               sigma=sigma)
-    delta = np.zeros(S.shape)
-    for k in range(samples):
-        r = SplitMix64Stream(1000 + seed + k, 7)
-        xs = np.floor(r.uniform(2 * S.size) * 3.0).reshape((2,) + S.shape) - 1.0
-        Sp = S.astype(np.float64) * (1.0 + 2.0 ** -23 * xs[0])
-        Mp = M.astype(np.float64) * (1.0 + 2.0 ** -23 * xs[1])
-        up = oracle.register(Sp, Mp, variant=variant, levels=levels, iters=iters, alpha=alpha,
-                             sigma=sigma)["u"]
-        delta = np.maximum(delta, np.abs(up - ref["u"]).max(axis=0))
-    return delta
+    up = oracle.register(S, M, variant=variant, levels=levels, iters=iters, alpha=alpha,
+                         sigma=sigma, round_f32=True)["u"]
+    return np.abs(up - ref["u"]).max(axis=0)
+
+
+def check32(oracle, S, M, g, ref, probe, label):
+    """Certified cases: the bar on every voxel.  Others: on probe-conditioned voxels."""
+    if probe.max() <= COND:
+        return compare(oracle, S, M, g, ref, label + " [certified]")
+    return compare(oracle, S, M, g, ref, label + " [masked]", probe)
 
 
 def compare(oracle, S, M, g, ref, label="", delta=None):
     """FP32 bar on the voxels conditioned for FP32 (all voxels if delta is None)."""
     err = np.abs(g["u"].astype(np.float64) - ref["u"]).max(axis=0)
-    mask = np.ones(err.shape, bool) if delta is None else (delta <= COND)
+    mask = np.ones(err.shape, bool) if delta is None else (delta <= COND_MASK)
     ill = 1.0 - float(mask.mean())
     assert ill <= MAX_ILL, f"{label}: {ill:.1%} of voxels ill-conditioned"
     du = float(err[mask].max()) if mask.any() else 0.0
@@ -121,17 +121,37 @@ CASES_VARIANT = [(0, 0.4), (1, 0.4), (2, 0.4), (3, 0.4), (4, 0.4), (4, 2.0), (5,
 
 @pytest.mark.parametrize("variant,alpha", CASES_VARIANT)
 def test_small_phantom_single_scale(dl, small_phantom, variant, alpha):
-    # 64 x 64 x 32 lung phantom, one level, 50 iterations, sigma 1
+    # 64 x 64 x 32 lung phantom, one level, sigma 1: 50 iterations, or 20 for the
+    # double and adjusted forces (conditioned there; 50 is checked below)
+    import oracle
+    S, M = small_phantom["S"], small_phantom["M"]
+    it = [20] if variant in (3, 4) else [50]
+    ref = oracle.register(S, M, variant=variant, levels=1, iters=it, alpha=alpha)
+    g64 = gpu_register(dl, S, M, variant, 1, it, alpha=alpha, fp64=True)
+    compare64(g64, ref, f"v{variant} a{alpha}")
+    g = gpu_register(dl, S, M, variant, 1, it, alpha=alpha)
+    probe = fp32_probe(S, M, variant, 1, it, alpha=alpha, ref=ref)
+    assert probe.max() <= COND, f"case not conditioned: probe {probe.max():.2e}"
+    check32(oracle, S, M, g, ref, probe, f"v{variant} a{alpha}")
+    assert g["stats"]["iters_run"] == it
+    assert g["stats"]["voxel_updates"] == 64 * 64 * 32 * it[0]
+
+
+@pytest.mark.parametrize("variant,alpha", [(3, 0.4), (4, 0.4), (4, 2.0)])
+def test_small_phantom_ill_conditioned_forces(dl, small_phantom, variant, alpha):
+    # 50 iterations of Eqs. (4)/(5): FP64 kernels match everywhere, FP32 on the
+    # voxels the probe shows conditioned
     import oracle
     S, M = small_phantom["S"], small_phantom["M"]
     ref = oracle.register(S, M, variant=variant, levels=1, iters=[50], alpha=alpha)
-    g64 = gpu_register(dl, S, M, variant, 1, [50], alpha=alpha, fp64=True)
-    compare64(g64, ref, f"v{variant} a{alpha}")
+    compare64(gpu_register(dl, S, M, variant, 1, [50], alpha=alpha, fp64=True), ref,
+              f"v{variant} a{alpha}")
     g = gpu_register(dl, S, M, variant, 1, [50], alpha=alpha)
-    delta = ulp_sensitivity(S, M, variant, 1, [50], alpha=alpha, ref=ref, samples=2)
-    compare(oracle, S, M, g, ref, f"v{variant} a{alpha}", delta if delta.max() > COND else None)
-    assert g["stats"]["iters_run"] == [50]
-    assert g["stats"]["voxel_updates"] == 64 * 64 * 32 * 50
+    probe = fp32_probe(S, M, variant, 1, [50], alpha=alpha, ref=ref)
+    du, rel, ill = check32(oracle, S, M, g, ref, probe, f"v{variant} a{alpha} 50 it")
+    err = np.abs(g["u"] - ref["u"]).max(axis=0)
+    print(f"v{variant} a{alpha} 50 it: probe max {probe.max():.2e}; FP32 max|du| "
+          f"{du:.2e} on {1 - ill:.2%} of voxels, {err.max():.2e} everywhere")
 
 
 @pytest.mark.parametrize("variant", range(6))
@@ -147,8 +167,8 @@ def test_ragged_multilevel(dl, variant, dims):
     ref = oracle.register(S, M, variant=variant, levels=3, iters=[12, 8, 6], alpha=0.4)
     compare64(gpu_register(dl, S, M, variant, 3, [12, 8, 6], fp64=True), ref, f"{dims} v{variant}")
     g = gpu_register(dl, S, M, variant, 3, [12, 8, 6], alpha=0.4)
-    delta = ulp_sensitivity(S, M, variant, 3, [12, 8, 6], ref=ref, samples=2)
-    compare(oracle, S, M, g, ref, f"{dims} v{variant}", delta if delta.max() > COND else None)
+    check32(oracle, S, M, g, ref, fp32_probe(S, M, variant, 3, [12, 8, 6], ref=ref),
+            f"{dims} v{variant}")
 
 
 @pytest.mark.parametrize("dims", [(5, 7, 3), (1, 9, 8), (13, 1, 6), (6, 5, 1), (2, 2, 2),
@@ -164,8 +184,8 @@ def test_degenerate_and_tiny(dl, dims, variant):
     ref = oracle.register(S, M, variant=variant, levels=levels, iters=iters, alpha=0.4)
     compare64(gpu_register(dl, S, M, variant, levels, iters, fp64=True), ref, f"{dims} v{variant}")
     g = gpu_register(dl, S, M, variant, levels, iters)
-    delta = ulp_sensitivity(S, M, variant, levels, iters, ref=ref, samples=2)
-    compare(oracle, S, M, g, ref, f"{dims} v{variant}", delta if delta.max() > COND else None)
+    check32(oracle, S, M, g, ref, fp32_probe(S, M, variant, levels, iters, ref=ref),
+            f"{dims} v{variant}")
 
 
 @pytest.mark.parametrize("sigma", [0.3, 0.6, 1.7, 2.6])
@@ -178,8 +198,8 @@ def test_other_sigmas(dl, sigma):
     ref = oracle.register(S, M, variant=3, levels=2, iters=[10, 10], sigma=sigma, alpha=0.4)
     compare64(gpu_register(dl, S, M, 3, 2, [10, 10], sigma=sigma, fp64=True), ref, f"s{sigma}")
     g = gpu_register(dl, S, M, 3, 2, [10, 10], sigma=sigma)
-    delta = ulp_sensitivity(S, M, 3, 2, [10, 10], sigma=sigma, ref=ref)
-    compare(oracle, S, M, g, ref, f"sigma {sigma}", delta if delta.max() > COND else None)
+    check32(oracle, S, M, g, ref, fp32_probe(S, M, 3, 2, [10, 10], sigma=sigma, ref=ref),
+            f"sigma {sigma}")
 
 
 def test_equal_images_give_zero_field(dl, small_phantom):
@@ -311,8 +331,8 @@ def test_full_size_parity(dl, full_phantom, variant, alpha):
     g64 = gpu_register(dl, S, M, variant, spacing=(0.9, 0.9, 2.5), fp64=True, **sched)
     compare64(g64, ref, f"full v{variant} a{alpha}")
     g = gpu_register(dl, S, M, variant, spacing=(0.9, 0.9, 2.5), **sched)
-    delta = ulp_sensitivity(S, M, variant, ref=ref, **sched)
-    du, rel, ill = compare(oracle, S, M, g, ref, f"full v{variant} a{alpha}", delta)
+    probe = fp32_probe(S, M, variant, ref=ref, **sched)
+    du, rel, ill = check32(oracle, S, M, g, ref, probe, f"full v{variant} a{alpha}")
     print(f"full v{variant} a{alpha}: FP32 max|du| {du:.2e} on conditioned voxels, "
           f"rel-RMS(W) {rel:.2e}, ill-conditioned {ill:.3%}, "
           f"max|du| everywhere {np.abs(g['u'] - ref['u']).max():.3e}")
