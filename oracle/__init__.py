@@ -63,7 +63,7 @@ def _lib(threaded: bool = False) -> C.CDLL:
         lib.or_register.restype = C.c_int
         lib.or_register.argtypes = ([_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.c_double, C.c_int, _ip, C.c_int, C.c_double, C.c_int, _dp,
-                                     _dp, _dp, _ip, _dp, C.c_int])
+                                     _dp, _dp, _ip, _dp, C.c_double, C.c_uint64])
         lib.or_num_threads.restype = C.c_int
         lib.or_num_threads.argtypes = []
         _LIBS[threaded] = lib
@@ -204,13 +204,14 @@ def ic_field(h) -> np.ndarray:
 def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: float = 1.0,
              alpha: float = 0.4, stop_mode: int = 0, eps: float = 1e-4, stop_window: int = 10,
              init=None, threaded: bool = True, return_raw: bool = False,
-             round_f32: bool = False):
+             probe_rel: float = 0.0, probe_seed: int = 0):
     """Whole registration.  `iters` lists iterations per level, coarsest first.
 
     Returns dict(u=(3, nz, ny, nx) field in voxels, stats=(n, 3) per-iteration
     [MSE, sum|du|, sum|u|], iters_run=list per level[, raw=iterated field]).
-    round_f32 rounds the field to float after every iteration: a conditioning
-    probe (how far single-precision storage alone moves the answer).
+    probe_rel > 0 injects relative noise of that size into the warped images
+    and the smoothed field every iteration (keyed by probe_seed): a probe of
+    how strongly the iteration amplifies rounding, not part of the method.
     """
     S = _f64(S)
     M = _f64(M)
@@ -226,7 +227,7 @@ def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: 
                                     float(sigma), int(levels), it, int(stop_mode), float(eps),
                                     int(stop_window), _p(ini) if ini is not None else None,
                                     _p(u), _p(stats), run, _p(raw) if raw is not None else None,
-                                    int(bool(round_f32)))
+                                    float(probe_rel), int(probe_seed))
     if rc != 0:
         raise ValueError(f"or_register failed: {rc}")
     runs = [int(run[i]) for i in range(levels)]

@@ -29,6 +29,8 @@
  *   or_force, or_iterate, or_register, or_ic_field  -- all pinned.
  *   The stop test (Sec. 2.4) is pinned only as a property; the paper prints no
  *   worked example of it.
+ *   or_register's conditioning probe (probe_rel > 0) is test instrumentation,
+ *   off by default; it is not used to compute any expected value.
  */
 #include <math.h>
 #include <stddef.h>
@@ -328,6 +330,32 @@ OR_EXPORT void or_force_arrays(int variant, double alpha, const double* d, const
 }
 
 /* ------------------------------------------------------------------------- */
+/* Conditioning probe (off unless or_register is asked for it): relative      */
+/* noise of rounding size on intermediate values, from SplitMix64 (Steele,    */
+/* Lea, Flood 2014) evaluated at a counter.                                   */
+/* ------------------------------------------------------------------------- */
+static struct {
+    double rel;
+    uint64_t key;
+} probe_now = {0.0, 0};
+
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static void probe_perturb(double* a, size_t n, uint64_t which) {
+    if (probe_now.rel == 0.0) return;
+    const uint64_t base = mix64(probe_now.key ^ (which * 0xD1B54A32D192ED03ull));
+    for (size_t c = 0; c < n; ++c) {
+        const uint64_t z = mix64(base + (uint64_t)(c + 1) * 0x9E3779B97F4A7C15ull);
+        const double xi = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+        a[c] *= 1.0 + probe_now.rel * xi;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* One demons iteration at one level (Fig. 1 flow: interpolation, gradient,   */
 /* displacement, low-pass filter, comparison).                                 */
 /*   S, M     static and moving image of the level                            */
@@ -359,6 +387,8 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     /* interpolation: W_m(x) = M(x + u); for Eq. (6) also W_s(x) = S(x - u) */
     or_warp(M, ux, uy, uz, nx, ny, nz, +1.0, W);
     if (ic) or_warp(S, ux, uy, uz, nx, ny, nz, -1.0, Ws);
+    probe_perturb(W, n, 1);
+    if (ic) probe_perturb(Ws, n, 2);
 
     /* gradient of the deformed image(s), recomputed every iteration (Sec. 2.2) */
     if (uses_gm) {
@@ -411,6 +441,9 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     int rc = or_gauss3(vx, ux, nx, ny, nz, sigma);
     rc |= or_gauss3(vy, uy, nx, ny, nz, sigma);
     rc |= or_gauss3(vz, uz, nx, ny, nz, sigma);
+    probe_perturb(ux, n, 3);
+    probe_perturb(uy, n, 4);
+    probe_perturb(uz, n, 5);
     return rc ? -3 : 0;
 }
 
@@ -455,17 +488,20 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /*   iters_run    per level (coarsest first), iterations actually run         */
 /*   raw_out      NULL, or 3 planar arrays of N doubles that receive the      */
 /*                iterated field itself (h for Eq. 6, equal to u_out else)    */
-/*   round_f32    0 normally.  1 rounds the field to the nearest float after  */
-/*                every iteration: a probe of how much storing the field in   */
-/*                single precision alone moves the result (conditioning test  */
-/*                of the iteration, not part of the method)                   */
+/*   probe_rel    0 normally.  > 0 turns on a conditioning probe that is not  */
+/*                part of the method: every iteration multiplies each warped  */
+/*                intensity and each smoothed field value by (1 + probe_rel * */
+/*                xi), xi uniform in [-1, 1) from a counter-based hash keyed  */
+/*                by probe_seed; probe_rel = 2^-24 models float rounding,     */
+/*                2^-53 double rounding                                       */
+/*   probe_seed   key of the probe's hash                                     */
 /* Returns 0 or a negative code.                                              */
 /* ------------------------------------------------------------------------- */
 OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, int nz,
                           int variant, double alpha, double sigma, int levels, const int* iters,
                           int stop_mode, double eps, int stop_window, const double* init,
                           double* u_out, double* stats, int* iters_run, double* raw_out,
-                          int round_f32) {
+                          double probe_rel, uint64_t probe_seed) {
     if (variant < 0 || variant > 5 || levels < 1 || levels > OR_MAX_LEVELS) return -1;
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     if (init && levels != 1) return -1;
@@ -549,12 +585,12 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
         int level_start = stat_at;
         for (int it = 0; it < iters[lc]; ++it) {
             double red[3];
+            probe_now.rel = probe_rel;
+            probe_now.key = probe_seed * 0x9E3779B97F4A7C15ull + (uint64_t)stat_at + 1;
             rc = or_iterate(variant, alpha, sigma, Sl[l], Ml[l], gsx, gsy, gsz,
                             variant == OR_EVOLVED_PASSIVE ? bm : NULL, ux, uy, uz, cx, cy, cz,
                             work, red);
             if (rc) break;
-            if (round_f32)
-                for (size_t c = 0; c < 3 * nl; ++c) u[c] = (double)(float)u[c];
             stats[3 * stat_at + 0] = red[0] / (double)nl;
             stats[3 * stat_at + 1] = red[1];
             stats[3 * stat_at + 2] = red[2];
@@ -581,6 +617,7 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
             memcpy(u_out, u, 3 * n0 * sizeof(double));
         }
     }
+    probe_now.rel = 0.0;
     for (int l = 0; l < levels; ++l) {
         free(Sl[l]);
         free(Ml[l]);

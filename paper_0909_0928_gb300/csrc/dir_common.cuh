@@ -43,6 +43,12 @@ __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float r_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double r_floor(double x) { return floor(x); }
 __device__ __forceinline__ float r_clamp(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+// division and vector norm as used by the single-precision path: the CUDA fast
+// intrinsics (about 2 ulp); the double-precision path stays exact
+__device__ __forceinline__ float r_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float r_norm_fast(float s) { return s > 0.0f ? s * rsqrtf(s) : 0.0f; }
+__device__ __forceinline__ double r_norm_fast(double s) { return sqrt(s); }
 __device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
 
 // One axis of the trilinear setup (Sec. 2.5 interpolation, clamped

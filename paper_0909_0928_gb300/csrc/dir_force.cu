@@ -40,7 +40,7 @@ __device__ __forceinline__ void term(Real d, Real gx, Real gy, Real gz, Real den
     if (den == Real(0)) {
         ox = oy = oz = Real(0);
     } else {
-        const Real c = d / den;
+        const Real c = r_div(d, den);
         ox = c * gx;
         oy = c * gy;
         oz = c * gz;
@@ -64,7 +64,7 @@ __device__ __forceinline__ void demons_force(Real d, Real gsx, Real gsy, Real gs
         if (den == Real(0)) {
             dx = dy = dz = Real(0);
         } else {
-            const Real c = Real(4) * d * a * b / den;
+            const Real c = r_div(Real(4) * d * a * b, den);
             dx = c * gsx;
             dy = c * gsy;
             dz = c * gsz;
@@ -83,7 +83,7 @@ __device__ __forceinline__ void demons_force(Real d, Real gsx, Real gsy, Real gs
 }
 
 template <typename Real, int V>
-__global__ void __launch_bounds__(FNT) force_kernel(const ForceArgs a) {
+__global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;  // uniform across the grid
     using T = VT<V>;
     const Grid3 g = a.g;
@@ -183,8 +183,8 @@ __global__ void __launch_bounds__(FNT) force_kernel(const ForceArgs a) {
                 dy = -dy;
                 dz = -dz;
                 sd2 += (double)(d * d);
-                sdu += (double)r_sqrt(dx * dx + dy * dy + dz * dz);
-                su += (double)r_sqrt(ux * ux + uy * uy + uz * uz);
+                sdu += (double)r_norm_fast(dx * dx + dy * dy + dz * dz);
+                su += (double)r_norm_fast(ux * ux + uy * uy + uz * uz);
                 v[o] = ux + dx;
                 v[o + cs] = uy + dy;
                 v[o + 2 * cs] = uz + dz;
