@@ -247,15 +247,18 @@ def main():
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    step_ms, force_ms, smooth_ms, nforce, launches = [], 0.0, 0.0, 0, 0
+    step_ms, launches = [], 0
+    kt = {"force": [0.0, 0], "fused": [0.0, 0], "smooth": [0.0, 0]}
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         st = step()
         ev[i][1].record(stream)
-        force_ms += st.ms_force_finest
-        smooth_ms += st.ms_smooth_finest
-        nforce += st.n_force_finest
+        for k, ms, n in (("force", st.ms_force_finest, st.n_force_finest),
+                         ("fused", st.ms_fused_finest, st.n_fused_finest),
+                         ("smooth", st.ms_smooth_finest, st.n_smooth_finest)):
+            kt[k][0] += ms
+            kt[k][1] += n
         launches += st.kernel_launches + 1
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -285,24 +288,31 @@ def main():
     e2e_s = e2e_s[args.warmup:]
     e2e_value = world * vu_step / statistics.mean(e2e_s)
 
-    # roofline of the dominant kernel (finest-level launches, timed live)
+    # roofline of the dominant kernel (finest-level launches, timed live);
+    # algorithmic bytes per voxel: force and fused iteration read the field
+    # (12), S (4) and M (4) and write the field (12); smoothing reads and writes
+    # the field (24)
     peak, peak_kind = measured_peak_gbs()
     n_fine = n0
-    favg = force_ms / max(nforce, 1)
-    savg = smooth_ms / max(nforce, 1)
-    if favg >= savg:
-        kname, bpv, avg_ms, src = "force_kernel", FORCE_BYTES[args.variant_id], favg, "dir_force.cu"
-    else:
-        kname, bpv, avg_ms, src = "smooth_kernel", SMOOTH_BYTES, savg, "dir_smooth.cu"
-    achieved = n_fine * bpv / (avg_ms / 1e3) / 1e9
-    traffic = profiled_traffic(kname, src)
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": n_fine * bpv, "avg_launch_ms": avg_ms,
+    bytes_pv = {"force": FORCE_BYTES[args.variant_id], "fused": FORCE_BYTES[args.variant_id],
+                "smooth": SMOOTH_BYTES}
+    src_of = {"force": "dir_force.cu", "fused": "dir_fused.cu", "smooth": "dir_smooth.cu"}
+    per_kernel = {}
+    for k, (ms, n) in kt.items():
+        if n:
+            avg = ms / n
+            per_kernel[k] = {"launches": n, "total_ms": ms, "avg_ms": avg,
+                             "achieved_gbs": n_fine * bytes_pv[k] / (avg / 1e3) / 1e9,
+                             "frac": n_fine * bytes_pv[k] / (avg / 1e3) / 1e9 / peak}
+    kname = max(per_kernel, key=lambda k: per_kernel[k]["total_ms"])
+    kk = per_kernel[kname]
+    traffic = profiled_traffic(kname + "_kernel", src_of[kname])
+    roofline = {"bound": "hbm", "kernel": kname + "_kernel", "achieved": kk["achieved_gbs"],
+                "peak": peak, "unit": "GB/s", "frac": kk["frac"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": n_fine * bytes_pv[kname],
+                "avg_launch_ms": kk["avg_ms"],
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
-                "force_avg_ms": favg, "smooth_avg_ms": savg,
-                "force_frac": n_fine * FORCE_BYTES[args.variant_id] / (favg / 1e3) / 1e9 / peak,
-                "smooth_frac": n_fine * SMOOTH_BYTES / (savg / 1e3) / 1e9 / peak}
+                "finest_level_kernels": per_kernel}
 
     per_variant = None
     if not args.no_variants:

@@ -88,6 +88,10 @@ typedef struct {
                                     DIR_F32 (default, the production path) or DIR_F64 (the same
                                     kernels in double precision, for verification against an
                                     FP64 reference where the iteration is ill-conditioned) */
+    int fuse;                    /* 1 (default): for Eqs. (1)-(2) without the stop test, fold the
+                                    Gaussian of iteration k into the force pass of iteration k+1
+                                    (same arithmetic, one pass over the field per iteration);
+                                    0: one force and one smoothing launch per iteration */
 } dir_params;
 
 typedef struct {
@@ -97,12 +101,16 @@ typedef struct {
     double mse_final;               /* the same before the last iteration run */
     double relnorm_final;           /* l(n) = sum|du| / sum|u| of the last iteration run (0 if undefined) */
     float ms_total;                 /* device time of the registration (CUDA events), ms */
-    float ms_force_finest;          /* with params.timing: summed force-kernel time at level 0, ms */
+    float ms_force_finest;          /* with params.timing: summed force-kernel time at level 0, ms
+                                       (the plain force pass: every iteration, or only the first
+                                       of a level when the smoothing is fused) */
     float ms_smooth_finest;         /* with params.timing: summed smoothing-kernel time at level 0, ms */
     int n_force_finest;             /* number of launches behind ms_force_finest */
     int n_smooth_finest;
     long long voxel_updates;        /* sum over levels of voxels * iterations run */
     int kernel_launches;            /* kernels launched by the registration (incl. early exits) */
+    float ms_fused_finest;          /* with params.timing: summed fused-iteration time at level 0, ms */
+    int n_fused_finest;             /* number of launches behind ms_fused_finest */
 } dir_stats;
 
 /* Fills *p with the defaults listed above.  Returns DIR_EINVAL if p is NULL. */

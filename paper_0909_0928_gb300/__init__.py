@@ -41,7 +41,7 @@ class DirParams(C.Structure):
                 ("alpha", C.c_double), ("stop_mode", C.c_int), ("eps", C.c_double),
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
                 ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("fuse", C.c_int)]
 
 
 class DirStats(C.Structure):
@@ -50,7 +50,8 @@ class DirStats(C.Structure):
                 ("relnorm_final", C.c_double), ("ms_total", C.c_float),
                 ("ms_force_finest", C.c_float), ("ms_smooth_finest", C.c_float),
                 ("n_force_finest", C.c_int), ("n_smooth_finest", C.c_int),
-                ("voxel_updates", C.c_longlong), ("kernel_launches", C.c_int)]
+                ("voxel_updates", C.c_longlong), ("kernel_launches", C.c_int),
+                ("ms_fused_finest", C.c_float), ("n_fused_finest", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"levels": self.levels, "iters_run": list(self.iters_run[: self.levels]),
@@ -59,7 +60,8 @@ class DirStats(C.Structure):
                 "ms_force_finest": self.ms_force_finest,
                 "ms_smooth_finest": self.ms_smooth_finest,
                 "n_force_finest": self.n_force_finest, "n_smooth_finest": self.n_smooth_finest,
-                "voxel_updates": self.voxel_updates, "kernel_launches": self.kernel_launches}
+                "voxel_updates": self.voxel_updates, "kernel_launches": self.kernel_launches,
+                "ms_fused_finest": self.ms_fused_finest, "n_fused_finest": self.n_fused_finest}
 
 
 class DirError(RuntimeError):

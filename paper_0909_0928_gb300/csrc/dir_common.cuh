@@ -52,28 +52,43 @@ __device__ __forceinline__ double r_norm_fast(double s) { return sqrt(s); }
 __device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
 
 // One axis of the trilinear setup (Sec. 2.5 interpolation, clamped
-// coordinates): lower corner floor(p) kept <= n-2 so the upper corner exists.
+// coordinates) at p = base + off, base an integer voxel index: clamp p to
+// [0, n-1], lower corner floor(p) kept <= n-2 so the upper corner exists,
+// weight p - corner.  Splitting p keeps the weight accurate to the precision
+// of the offset rather than of base + off (single precision at base = 255
+// would otherwise round p to about 3e-5 voxel).
 template <typename Real>
-__device__ __forceinline__ void axis_setup(Real p, int n, int& i0, int& i1, Real& f) {
-    p = r_clamp(p, Real(0), Real(n - 1));
-    int lo = (int)r_floor(p);
-    lo = min(lo, n - 2);
-    lo = max(lo, 0);
-    i0 = lo;
-    i1 = (n > 1) ? lo + 1 : lo;
-    f = p - (Real)lo;
+__device__ __forceinline__ void axis_setup(int base, Real off, int n, int& i0, int& i1, Real& f) {
+    const Real fl = r_floor(r_clamp(off, Real(-1048576), Real(1048576)));
+    const int i = base + (int)fl;
+    if (n < 2) {
+        i0 = i1 = 0;
+        f = Real(0);
+    } else if (i < 0) {                       // p < 0: clamped to 0
+        i0 = 0;
+        i1 = 1;
+        f = Real(0);
+    } else if (i >= n - 1) {                  // p >= n-1: clamped to n-1
+        i0 = n - 2;
+        i1 = n - 1;
+        f = Real(1);
+    } else {
+        i0 = i;
+        i1 = i + 1;
+        f = off - fl;
+    }
 }
 
-// Software trilinear interpolation of a pitched volume at a continuous voxel
-// position (x, y, z); lerps along x, then y, then z.
+// Software trilinear interpolation of a pitched volume at the continuous voxel
+// position (bx + ox, by + oy, bz + oz); lerps along x, then y, then z.
 template <typename Real>
-__device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid3& g, Real x,
-                                          Real y, Real z) {
+__device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid3& g, int bx,
+                                          Real ox, int by, Real oy, int bz, Real oz) {
     int x0, x1, y0, y1, z0, z1;
     Real fx, fy, fz;
-    axis_setup(x, g.nx, x0, x1, fx);
-    axis_setup(y, g.ny, y0, y1, fy);
-    axis_setup(z, g.nz, z0, z1, fz);
+    axis_setup(bx, ox, g.nx, x0, x1, fx);
+    axis_setup(by, oy, g.ny, y0, y1, fy);
+    axis_setup(bz, oz, g.nz, z0, z1, fz);
     const Real* p00 = I + (long long)g.px * y0 + g.plane * z0;
     const Real* p10 = I + (long long)g.px * y1 + g.plane * z0;
     const Real* p01 = I + (long long)g.px * y0 + g.plane * z1;

@@ -94,6 +94,7 @@ struct dir_ctx {
     int* derr = nullptr;
     int total_iters = 0;
     int level_first[DIR_MAX_LEVELS];
+    int fused_level[DIR_MAX_LEVELS];
     char* final_field = nullptr;
     bool have_field = false;
     bool pending = false;
@@ -246,7 +247,61 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         sa.stop_iter = c->ctl + lc;
         sa.err = c->derr;
         const bool timed = c->p.timing && l == 0;
-        for (int it = 0; it < c->p.iters[lc]; ++it, ++row) {
+        const int n = c->p.iters[lc];
+        const bool fused = c->p.fuse && c->p.stop_mode == 0 && dirk::fused_supported(c->variant);
+        if (fused && n > 0) {
+            // iteration 0 from u, iterations 1..n-1 from the previous v with the
+            // smoothing folded in, then one smoothing of the last v
+            char* vbuf = oth;
+            char* spare = cur;
+            for (int it = 0; it < n; ++it, ++row) {
+                cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
+                if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
+                if (it == 0) {
+                    fa.u = cur;
+                    fa.v = vbuf;
+                    fa.red = c->red + 3 * (size_t)row;
+                    fa.iter = it;
+                    CK(c, dirk::launch_force(c->variant, f64, fa, s));
+                } else {
+                    dirk::FusedArgs ua;
+                    ua.S = c->lv[l].S;
+                    ua.M = c->lv[l].M;
+                    ua.vin = vbuf;
+                    ua.v = spare;
+                    ua.g = g;
+                    ua.taps = c->taps;
+                    ua.red = c->red + 3 * (size_t)row;
+                    ua.stop_iter = c->ctl + lc;
+                    ua.iter = it;
+                    ua.err = c->derr;
+                    CK(c, dirk::launch_fused(c->variant, f64, ua, c->num_sms, s));
+                    char* t = vbuf;
+                    vbuf = spare;
+                    spare = t;
+                }
+                c->launches += 1;
+                if (timed) {
+                    if (record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
+                    if (it < n - 1 && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
+                }
+                if (it == n - 1) {
+                    sa.in = vbuf;
+                    sa.out = spare;
+                    sa.iter = it;
+                    CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
+                    c->launches += 1;
+                    if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
+                    cur = spare;
+                    oth = vbuf;
+                }
+                if (timed) c->n_timed += 1;
+            }
+            c->fused_level[lc] = 1;
+            continue;
+        }
+        c->fused_level[lc] = 0;
+        for (int it = 0; it < n; ++it, ++row) {
             cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
             if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
             fa.u = cur;
@@ -339,6 +394,7 @@ static int validate_params(const dir_params* p) {
     if (p->field_dtype != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->precision != DIR_F32 && p->precision != DIR_F64) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
+    if (p->fuse != 0 && p->fuse != 1) return DIR_EINVAL;
     return DIR_OK;
 }
 
@@ -361,6 +417,7 @@ int dir_params_default(dir_params* p) {
     p->use_graph = 1;
     p->timing = 0;
     p->precision = DIR_F32;
+    p->fuse = 1;
     return DIR_OK;
 }
 
@@ -581,14 +638,22 @@ int dir_sync(dir_ctx* c, dir_stats* st) {
         st->kernel_launches = c->launches;
         if (c->p.timing) {
             const int runs = c->iters_run[fin];
+            const bool fused = c->fused_level[fin] != 0;
             for (int i = 0; i < c->n_timed && i < runs; ++i) {
                 float a = 0.f, b = 0.f;
                 CK(c, cudaEventElapsedTime(&a, c->tev[3 * i], c->tev[3 * i + 1]));
                 CK(c, cudaEventElapsedTime(&b, c->tev[3 * i + 1], c->tev[3 * i + 2]));
-                st->ms_force_finest += a;
-                st->ms_smooth_finest += b;
-                st->n_force_finest += 1;
-                st->n_smooth_finest += 1;
+                if (fused && i > 0) {
+                    st->ms_fused_finest += a;
+                    st->n_fused_finest += 1;
+                } else {
+                    st->ms_force_finest += a;
+                    st->n_force_finest += 1;
+                }
+                if (!fused || i == runs - 1) {
+                    st->ms_smooth_finest += b;
+                    st->n_smooth_finest += 1;
+                }
             }
         }
     }

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "dir_common.cuh"
+#include "dir_force_law.cuh"
 #include "dir_launch.h"
 
 namespace dirk {
@@ -33,54 +34,6 @@ struct VT {
     static constexpr bool IC = (V == 5);
     static constexpr bool EV = (V == 1);
 };
-
-template <typename Real>
-__device__ __forceinline__ void term(Real d, Real gx, Real gy, Real gz, Real den, Real& ox,
-                                     Real& oy, Real& oz) {
-    if (den == Real(0)) {
-        ox = oy = oz = Real(0);
-    } else {
-        const Real c = r_div(d, den);
-        ox = c * gx;
-        oy = c * gy;
-        oz = c * gz;
-    }
-}
-
-// dr of Eqs. (1)-(6).  gs: static gradient, gm: warped-image gradient (for
-// Eq. 6 the gradient of W_m + W_s), b: |grad M| on the grid (Eq. 2).
-template <typename Real, int V>
-__device__ __forceinline__ void demons_force(Real d, Real gsx, Real gsy, Real gsz, Real gmx,
-                                             Real gmy, Real gmz, Real b, Real alpha2, Real& dx,
-                                             Real& dy, Real& dz) {
-    const Real d2 = d * d;
-    if (V == 0) {
-        term(d, gsx, gsy, gsz, d2 + (gsx * gsx + gsy * gsy + gsz * gsz), dx, dy, dz);
-    } else if (V == 1) {
-        const Real gs2 = gsx * gsx + gsy * gsy + gsz * gsz;
-        const Real a = r_sqrt(gs2);
-        const Real s = a * a + b * b;
-        const Real den = (Real(2) * d2 + s) * s;
-        if (den == Real(0)) {
-            dx = dy = dz = Real(0);
-        } else {
-            const Real c = r_div(Real(4) * d * a * b, den);
-            dx = c * gsx;
-            dy = c * gsy;
-            dz = c * gsz;
-        }
-    } else if (V == 2 || V == 5) {
-        term(d, gmx, gmy, gmz, d2 + (gmx * gmx + gmy * gmy + gmz * gmz), dx, dy, dz);
-    } else {
-        const Real ad2 = (V == 4) ? alpha2 * d2 : d2;
-        Real px, py, pz, qx, qy, qz;
-        term(d, gsx, gsy, gsz, ad2 + (gsx * gsx + gsy * gsy + gsz * gsz), px, py, pz);
-        term(d, gmx, gmy, gmz, ad2 + (gmx * gmx + gmy * gmy + gmz * gmz), qx, qy, qz);
-        dx = px + qx;
-        dy = py + qy;
-        dz = pz + qz;
-    }
-}
 
 template <typename Real, int V>
 __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
@@ -115,9 +68,9 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
             const int gz = clampi(bz0 + hz - 1, 0, g.nz - 1);
             const long long o = offs(g, gx, gy, gz);
             const Real ux = __ldg(u + o), uy = __ldg(u + o + cs), uz = __ldg(u + o + 2 * cs);
-            const Real wm = trilinear(M, g, (Real)gx + ux, (Real)gy + uy, (Real)gz + uz);
+            const Real wm = trilinear(M, g, gx, ux, gy, uy, gz, uz);
             if (T::IC) {
-                const Real ws = trilinear(S, g, (Real)gx - ux, (Real)gy - uy, (Real)gz - uz);
+                const Real ws = trilinear(S, g, gx, -ux, gy, -uy, gz, -uz);
                 Wt[hz][hy][hx] = wm + ws;
                 if (hx >= 1 && hx <= FTX && hy >= 1 && hy <= FTY && hz >= 1 && hz <= FTZ)
                     Dt[T::IC ? hz - 1 : 0][hy - 1][hx - 1] = wm - ws;
@@ -174,7 +127,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
                     else
                         d = Wt[k + 1][ty + 1][tx + 1] - (T::GS ? scol[k + 1] : __ldg(S + o));
                 } else {
-                    const Real w = trilinear(M, g, (Real)x + ux, (Real)y + uy, (Real)z + uz);
+                    const Real w = trilinear(M, g, x, ux, y, uy, z, uz);
                     d = w - scol[k + 1];
                 }
                 Real dx, dy, dz;

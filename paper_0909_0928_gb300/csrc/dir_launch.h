@@ -40,6 +40,23 @@ struct SmoothArgs {
 };
 cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s);
 
+// One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
+// force kernel's work, v = u - dr(u); red as for ForceArgs.
+struct FusedArgs {
+    const void* S;
+    const void* M;
+    const void* vin;     // v of the previous iteration (3 components)
+    void* v;             // v of this iteration
+    Grid3 g;
+    Taps taps;
+    double* red;
+    const int* stop_iter;
+    int iter;
+    int* err;
+};
+bool fused_supported(int variant);
+cudaError_t launch_fused(int variant, bool fp64, const FusedArgs& a, int num_sms, cudaStream_t s);
+
 // out(i, j, k) = in(2i, 2j, 2k)   (pyramid decimation, Sec. 2.3)
 cudaError_t launch_decimate(bool fp64, const void* in, const Grid3& gin, void* out,
                             const Grid3& gout, cudaStream_t s);

@@ -31,11 +31,13 @@ __global__ void upsample_kernel(const Real* __restrict__ coarse, Grid3 gc, Real*
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= gf.nx || y >= gf.ny) return;
-    const Real cx = Real(0.5) * x, cy = Real(0.5) * y, cz = Real(0.5) * z;
+    // coarse position x / 2 = (x >> 1) + (x & 1) / 2, exact
+    const Real hx = Real(0.5) * (x & 1), hy = Real(0.5) * (y & 1), hz = Real(0.5) * (z & 1);
     const long long o = offs(gf, x, y, z);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        fine[o + c * gf.cs] = Real(2) * trilinear(coarse + c * gc.cs, gc, cx, cy, cz);
+        fine[o + c * gf.cs] =
+            Real(2) * trilinear(coarse + c * gc.cs, gc, x >> 1, hx, y >> 1, hy, z >> 1, hz);
 }
 
 template <typename Real>
@@ -45,8 +47,8 @@ __global__ void warp_kernel(const Real* __restrict__ img, const Real* __restrict
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long o = offs(g, x, y, z);
-    const Real w = trilinear(img, g, (Real)x + __ldg(u + o), (Real)y + __ldg(u + o + g.cs),
-                             (Real)z + __ldg(u + o + 2 * g.cs));
+    const Real w = trilinear(img, g, x, __ldg(u + o), y, __ldg(u + o + g.cs), z,
+                             __ldg(u + o + 2 * g.cs));
     out[(long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z)] = (float)w;
 }
 
@@ -59,19 +61,20 @@ __global__ void ic_invert_kernel(const Real* __restrict__ h, Real* __restrict__ 
     const Real* hx = h;
     const Real* hy = h + g.cs;
     const Real* hz = h + 2 * g.cs;
-    Real px = (Real)x, py = (Real)y, pz = (Real)z;
+    // x* = y + a with a = h(x*), iterated from a = 0
+    Real ax = 0, ay = 0, az = 0;
     for (int s = 0; s < steps; ++s) {
-        const Real ax = trilinear(hx, g, px, py, pz);
-        const Real ay = trilinear(hy, g, px, py, pz);
-        const Real az = trilinear(hz, g, px, py, pz);
-        px = (Real)x + ax;
-        py = (Real)y + ay;
-        pz = (Real)z + az;
+        const Real nx_ = trilinear(hx, g, x, ax, y, ay, z, az);
+        const Real ny_ = trilinear(hy, g, x, ax, y, ay, z, az);
+        const Real nz_ = trilinear(hz, g, x, ax, y, ay, z, az);
+        ax = nx_;
+        ay = ny_;
+        az = nz_;
     }
     const long long o = offs(g, x, y, z);
-    u[o] = Real(2) * trilinear(hx, g, px, py, pz);
-    u[o + g.cs] = Real(2) * trilinear(hy, g, px, py, pz);
-    u[o + 2 * g.cs] = Real(2) * trilinear(hz, g, px, py, pz);
+    u[o] = Real(2) * trilinear(hx, g, x, ax, y, ay, z, az);
+    u[o + g.cs] = Real(2) * trilinear(hy, g, x, ax, y, ay, z, az);
+    u[o + 2 * g.cs] = Real(2) * trilinear(hz, g, x, ax, y, ay, z, az);
 }
 
 template <typename Real, typename Out>

@@ -1,0 +1,262 @@
+// dir_stencil.cuh -- the separable Gaussian's building blocks (Sec. 2.5 low-pass
+// filter), shared by the smoothing kernel and the fused iteration kernel.
+//
+// A block owns a 32 x 8 (x, y) column tile and marches through a chunk of z
+// planes.  Each input plane's tile plus halo arrives by TMA
+// (cp.async.bulk.tensor, all components in one copy) into a 4-slot ring of
+// shared memory several planes ahead; out-of-volume halo cells (zero-filled by
+// the copy) are overwritten with the nearest edge voxel (replicate boundary);
+// the x pass filters 4 adjacent outputs per task from 128-bit shared loads;
+// the y pass filters 4 rows of one column of one component per thread into a
+// rolling register window of 2R+1 planes, from which the z pass is taken.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "dir_common.cuh"
+#include "dir_launch.h"
+
+namespace dirk {
+
+constexpr int STX = 32, STY = 8, STAGES = 4, YW = 4;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+template <typename Real>
+struct Vec16;  // 16-byte vector of Real
+template <>
+struct Vec16<float> {
+    using T = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    static constexpr int N = 2;
+};
+
+__device__ __forceinline__ void unpack(const float4& t, float* d) {
+    d[0] = t.x;
+    d[1] = t.y;
+    d[2] = t.z;
+    d[3] = t.w;
+}
+__device__ __forceinline__ void unpack(const double2& t, double* d) {
+    d[0] = t.x;
+    d[1] = t.y;
+}
+__device__ __forceinline__ void store4(float* dst, const float* s) {
+    *reinterpret_cast<float4*>(dst) = make_float4(s[0], s[1], s[2], s[3]);
+}
+__device__ __forceinline__ void store4(double* dst, const double* s) {
+    reinterpret_cast<double2*>(dst)[0] = make_double2(s[0], s[1]);
+    reinterpret_cast<double2*>(dst)[1] = make_double2(s[2], s[3]);
+}
+
+template <typename Real, int R, int NC>
+struct StencilGeom {
+    static constexpr int HA = (R + 3) / 4 * 4;   // x halo rounded up: TMA x start 16-byte aligned
+    static constexpr int WB = STX + 2 * HA;      // box width
+    static constexpr int H = STY + 2 * R;        // box height
+    static constexpr int K = 2 * R + 1;
+    static constexpr int YT = STX * NC * (STY / YW);  // y/z tasks: (x, component, row group)
+    static constexpr int XL = 4 + 2 * R;              // inputs of one 4-output x task
+    static constexpr int XLV = (HA - R + XL + 3) / 4 * 4;  // loaded span, whole 16-byte vectors
+    static constexpr int SLOT_ELEMS = NC * H * WB;
+    static constexpr int SLOT_BYTES = SLOT_ELEMS * (int)sizeof(Real);
+    static constexpr int SLOT_STRIDE = (SLOT_BYTES + 127) / 128 * 128;
+    static constexpr int TXP_BYTES = NC * H * STX * (int)sizeof(Real);
+    static constexpr int TXP_STRIDE = (TXP_BYTES + 127) / 128 * 128;
+    // dynamic shared memory: align slack, slots, x-pass rows, barriers, extra
+    static constexpr int BASE_SMEM = 128 + STAGES * SLOT_STRIDE + TXP_STRIDE + 64;
+};
+
+// Per-block state of the TMA plane pipeline.
+template <typename Real, int R, int NC>
+struct PlanePipe {
+    using G = StencilGeom<Real, R, NC>;
+    unsigned char* base;
+    Real* txp;
+    uint64_t* full;
+    int z0, nsteps, bx, by;
+    bool edge;
+
+    __device__ void setup(unsigned char* smem_raw, const Grid3& g, int x0, int y0, int zstart,
+                          int zend) {
+        base = reinterpret_cast<unsigned char*>(
+            (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+        txp = reinterpret_cast<Real*>(base + STAGES * G::SLOT_STRIDE);
+        full = reinterpret_cast<uint64_t*>(base + STAGES * G::SLOT_STRIDE + G::TXP_STRIDE);
+        z0 = zstart;
+        nsteps = (zend - zstart) + 2 * R;  // input planes z0-R .. z1-1+R (clamped)
+        bx = x0 - G::HA;
+        by = y0 - R;
+        edge = (bx < 0) || (bx + G::WB > g.nx) || (by < 0) || (by + G::H > g.ny);
+    }
+    __device__ unsigned char* extra() const {
+        return base + STAGES * G::SLOT_STRIDE + G::TXP_STRIDE + 64;
+    }
+    __device__ void issue(const CUtensorMap* map, const Grid3& g, int step) {
+        const int s = step % STAGES;
+        const int pc = clampi(z0 - R + step, 0, g.nz - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[s], (uint32_t)G::SLOT_BYTES);
+        tma_load_4d(base + s * G::SLOT_STRIDE, map, bx, by, pc, 0, &full[s]);
+    }
+    // thread 0: init barriers and prefetch; everyone: barrier
+    __device__ void start(const CUtensorMap* map, const Grid3& g, int tid) {
+        if (tid == 0) {
+            for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+            fence_mbar_init();
+            fence_proxy_async();
+            for (int st = 0; st < STAGES - 1 && st < nsteps; ++st) issue(map, g, st);
+        }
+        __syncthreads();
+    }
+    // Step `step`: refill, wait for the slot (bounded), fix edges, x pass.
+    // Returns false (for every thread) if the copy never arrived.
+    template <int NT>
+    __device__ bool xpass(const CUtensorMap* map, const Grid3& g, int step, int tid,
+                          const Real* w, int* err) {
+        if (tid == 0 && step + STAGES - 1 < nsteps) issue(map, g, step + STAGES - 1);
+        const int s = step % STAGES;
+        const uint32_t parity = (uint32_t)((step / STAGES) & 1);
+        // one thread spins (bounded); after the barrier every thread observes
+        // the completed phase once, which makes the copied bytes visible to it
+        bool ok = true;
+        if (tid == 0) ok = mbar_wait_bounded(&full[s], parity, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && err) atomicOr(err, kErrTmaTimeout);
+            return false;
+        }
+        (void)mbar_try_wait(&full[s], parity);
+        constexpr int HA = G::HA, WB = G::WB, H = G::H, K = G::K;
+        using V = typename Vec16<Real>::T;
+        constexpr int VN = Vec16<Real>::N;
+        Real* slot = reinterpret_cast<Real*>(base + s * G::SLOT_STRIDE);  // [NC][H][WB]
+        if (edge) {
+            // replicate boundary: out-of-volume columns first (a thread per
+            // row), then out-of-volume rows (a thread per column, rows already
+            // column-fixed)
+            const int lo = max(0, -bx);         // first in-volume column of the box
+            const int hi = min(WB, g.nx - bx);  // one past the last
+            for (int row = tid; row < NC * H; row += NT) {
+                Real* r = slot + row * WB;
+                const Real left = r[lo], right = r[hi - 1];
+                for (int hx = 0; hx < lo; ++hx) r[hx] = left;
+                for (int hx = hi; hx < WB; ++hx) r[hx] = right;
+            }
+            __syncthreads();
+            const int rlo = max(0, -by);
+            const int rhi = min(H, g.ny - by);
+            for (int col = tid; col < NC * WB; col += NT) {
+                Real* cbase = slot + (col / WB) * H * WB + (col % WB);
+                const Real top = cbase[rlo * WB], bot = cbase[(rhi - 1) * WB];
+                for (int hy = 0; hy < rlo; ++hy) cbase[hy * WB] = top;
+                for (int hy = rhi; hy < H; ++hy) cbase[hy * WB] = bot;
+            }
+            __syncthreads();
+        }
+        for (int tk = tid; tk < NC * H * (STX / 4); tk += NT) {
+            const int gq = tk % (STX / 4);
+            const int row = tk / (STX / 4);  // c * H + r
+            const Real* src = slot + row * WB + 4 * gq;  // 16-byte aligned
+            Real in[G::XLV];
+#pragma unroll
+            for (int v = 0; v < G::XLV / VN; ++v) unpack(reinterpret_cast<const V*>(src)[v], in + v * VN);
+            Real o[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                Real acc = Real(0);
+#pragma unroll
+                for (int t = 0; t < K; ++t) acc += w[t] * in[HA - R + j + t];
+                o[j] = acc;
+            }
+            store4(txp + row * STX + 4 * gq, o);
+        }
+        __syncthreads();
+        return true;
+    }
+    // y pass of rows q*YW .. q*YW+YW-1 of column lx, component c, into the ring
+    __device__ void ypass(int c, int q, int lx, const Real* w, Real (&ring)[G::K][YW]) const {
+        constexpr int H = G::H, K = G::K;
+        const Real* col = txp + (c * H + q * YW) * STX + lx;
+        Real in[YW + 2 * R];
+#pragma unroll
+        for (int k = 0; k < YW + 2 * R; ++k) in[k] = col[k * STX];
+#pragma unroll
+        for (int t = 0; t < K - 1; ++t)
+#pragma unroll
+            for (int r = 0; r < YW; ++r) ring[t][r] = ring[t + 1][r];
+#pragma unroll
+        for (int r = 0; r < YW; ++r) {
+            Real acc = Real(0);
+#pragma unroll
+            for (int t = 0; t < K; ++t) acc += w[t] * in[r + t];
+            ring[K - 1][r] = acc;
+        }
+    }
+};
+
+template <typename Real, int R>
+__device__ __forceinline__ Real zpass(const Real* w, const Real (&ring)[2 * R + 1][YW], int r) {
+    Real acc = Real(0);
+#pragma unroll
+    for (int t = 0; t < 2 * R + 1; ++t) acc += w[t] * ring[t][r];
+    return acc;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a pitched (x, y, z, component) array with the plane box of
+// StencilGeom<Real, R, NC>.  Returns false if the driver refuses it.
+template <typename Real, int R, int NC>
+inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g) {
+    using G = StencilGeom<Real, R, NC>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                                (cuuint64_t)NC};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * sizeof(Real),
+                                   (cuuint64_t)g.plane * sizeof(Real),
+                                   (cuuint64_t)g.cs * sizeof(Real)};
+    const cuuint32_t box[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, 1u, (cuuint32_t)NC};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    return enc(map, sizeof(Real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+               4, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// z chunk: as many chunks as fit in one wave of resident blocks (a partial
+// second wave would leave most SMs idle while it runs); short chunks (down to
+// one plane) for small volumes so that enough blocks run
+inline int stencil_zchunk(const Grid3& g, int blocks_per_sm, int num_sms) {
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    const long long bxy = (long long)((g.nx + STX - 1) / STX) * ((g.ny + STY - 1) / STY);
+    const long long wave = (long long)blocks_per_sm * num_sms;
+    long long chunks = wave / bxy;
+    if (chunks < 1) chunks = 1;
+    if (chunks > g.nz) chunks = g.nz;
+    const int zc = (int)((g.nz + chunks - 1) / chunks);
+    return zc < 1 ? 1 : zc;
+}
+
+}  // namespace dirk

@@ -49,10 +49,10 @@ def dl():
 
 def gpu_register(dl, S, M, variant, levels, iters, alpha=0.4, sigma=1.0, spacing=(1, 1, 2.5),
                  stop_mode=0, eps=1e-4, window=10, use_graph=1, on_device=True, init=None,
-                 timing=0, repeat=1, fp64=False):
+                 timing=0, repeat=1, fp64=False, fuse=1):
     params = dl.dir_params_default(levels=levels, iters=iters, alpha=alpha, sigma=sigma,
                                    stop_mode=stop_mode, eps=eps, stop_window=window,
-                                   use_graph=use_graph, timing=timing,
+                                   use_graph=use_graph, timing=timing, fuse=fuse,
                                    precision=dl.DIR_F64 if fp64 else dl.DIR_F32)
     keep = None
     if init is not None:
@@ -316,15 +316,36 @@ def test_state_errors(dl, small_phantom):
     assert e.value.code == dlm.DIR_EINVAL
 
 
-def test_timing_stats(dl, small_phantom):
+@pytest.mark.parametrize("fuse", [1, 0])
+def test_timing_stats(dl, small_phantom, fuse):
     S, M = small_phantom["S"], small_phantom["M"]
     for graph in (1, 0):
-        g = gpu_register(dl, S, M, 0, 2, [4, 7], timing=1, use_graph=graph)
+        g = gpu_register(dl, S, M, 0, 2, [4, 7], timing=1, use_graph=graph, fuse=fuse)
         st = g["stats"]
-        assert st["n_force_finest"] == 7 and st["n_smooth_finest"] == 7
+        if fuse:
+            # per level: plain force, fused iterations, one smoothing
+            assert st["n_force_finest"] == 1 and st["n_fused_finest"] == 6
+            assert st["n_smooth_finest"] == 1
+            assert st["kernel_launches"] == 2 * 2 + 1 + (4 + 1) + (7 + 1)
+            assert 0 < st["ms_fused_finest"] < st["ms_total"]
+        else:
+            assert st["n_force_finest"] == 7 and st["n_smooth_finest"] == 7
+            assert st["n_fused_finest"] == 0
+            assert st["kernel_launches"] == 2 * 2 + 1 + 2 * 11
         assert 0 < st["ms_force_finest"] < st["ms_total"]
         assert 0 < st["ms_smooth_finest"] < st["ms_total"]
-        assert st["kernel_launches"] == 2 * 2 + 1 + 2 * 11
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_fused_schedule_matches_two_kernel_schedule(dl, small_phantom, variant, fp64):
+    # folding the Gaussian into the next force pass changes no arithmetic
+    S, M = small_phantom["S"], small_phantom["M"]
+    a = gpu_register(dl, S, M, variant, 3, [20, 10, 5], fuse=1, fp64=fp64)
+    b = gpu_register(dl, S, M, variant, 3, [20, 10, 5], fuse=0, fp64=fp64)
+    diff = float(np.abs(a["u"].astype(np.float64) - b["u"]).max())
+    assert diff <= (1e-12 if fp64 else 1e-5), diff
+    np.testing.assert_allclose(a["hist"], b["hist"], rtol=1e-5 if not fp64 else 1e-12)
 
 
 # ------------------------------------------------------------- full size
