@@ -317,8 +317,9 @@ def main():
     per_variant = None
     if not args.no_variants:
         per_variant = {}
-        for vid, alpha in ((0, 0.4), (1, 0.4), (2, 0.4), (3, 0.4), (4, 0.4), (4, 2.0), (5, 0.4)):
-            p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha)
+        for vid, alpha, fuse in ((0, 0.4, 1), (0, 0.4, 0), (1, 0.4, 1), (2, 0.4, 1), (3, 0.4, 1),
+                                 (4, 0.4, 1), (4, 2.0, 1), (5, 0.4, 1)):
+            p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, fuse=fuse)
             c2 = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, vid, p2, stream)
             ms = []
             for k in range(8):
@@ -327,7 +328,8 @@ def main():
                 if k >= 3:
                     ms.append(st.ms_total)
             dl.dir_destroy(c2)
-            name = VARIANT_NAMES[vid] + (f"_alpha{alpha}" if vid == 4 else "")
+            name = VARIANT_NAMES[vid] + (f"_alpha{alpha}" if vid == 4 else "") + \
+                ("" if fuse or vid > 1 else "_unfused")
             med = statistics.median(ms)
             per_variant[name] = {"ms_p50": med, "voxel_updates_per_s": vu_step / (med / 1e3)}
 

@@ -34,8 +34,10 @@ constexpr int kErrTmaTimeout = 1;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-__device__ __forceinline__ long long offs(const Grid3& g, int i, int j, int k) {
-    return (long long)i + (long long)g.px * j + g.plane * k;
+// 32-bit element offsets: the engine bounds volumes so that every field
+// offset (three components included) stays below 2^31
+__device__ __forceinline__ int offs(const Grid3& g, int i, int j, int k) {
+    return i + g.px * j + (int)g.plane * k;
 }
 
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
@@ -89,10 +91,11 @@ __device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid
     axis_setup(bx, ox, g.nx, x0, x1, fx);
     axis_setup(by, oy, g.ny, y0, y1, fy);
     axis_setup(bz, oz, g.nz, z0, z1, fz);
-    const Real* p00 = I + (long long)g.px * y0 + g.plane * z0;
-    const Real* p10 = I + (long long)g.px * y1 + g.plane * z0;
-    const Real* p01 = I + (long long)g.px * y0 + g.plane * z1;
-    const Real* p11 = I + (long long)g.px * y1 + g.plane * z1;
+    const int pl = (int)g.plane;
+    const Real* p00 = I + (g.px * y0 + pl * z0);
+    const Real* p10 = I + (g.px * y1 + pl * z0);
+    const Real* p01 = I + (g.px * y0 + pl * z1);
+    const Real* p11 = I + (g.px * y1 + pl * z1);
     const Real c000 = __ldg(p00 + x0), c100 = __ldg(p00 + x1);
     const Real c010 = __ldg(p10 + x0), c110 = __ldg(p10 + x1);
     const Real c001 = __ldg(p01 + x0), c101 = __ldg(p01 + x1);
@@ -107,30 +110,33 @@ __device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid
     return v0 * gz + v1 * fz;
 }
 
-// Block-wide sum of three per-thread values in double, then one FP64 atomic
-// per value.  Every thread of the block must call it.
-template <int NT>
-__device__ __forceinline__ void block_reduce3_atomic(double da, double db, double dc, double* out) {
+// Block-wide sum of three per-thread partial sums, then one FP64 atomic per
+// value.  Within a warp the sums stay in the working precision (float for the
+// production path: 32 partials of a few voxels each); across warps and blocks
+// they are added in double (the global MSE / convergence reduction).  Every
+// thread of the block must call it.
+template <int NT, typename Real>
+__device__ __forceinline__ void block_reduce3_atomic(Real a, Real b, Real c, double* out) {
     static_assert(NT % 32 == 0, "block size must be whole warps");
     __shared__ double red_s[3][NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        da += __shfl_down_sync(0xffffffffu, da, o);
-        db += __shfl_down_sync(0xffffffffu, db, o);
-        dc += __shfl_down_sync(0xffffffffu, dc, o);
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
     }
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) {
-        red_s[0][warp] = da;
-        red_s[1][warp] = db;
-        red_s[2][warp] = dc;
+        red_s[0][warp] = (double)a;
+        red_s[1][warp] = (double)b;
+        red_s[2][warp] = (double)c;
     }
     __syncthreads();
     if (warp == 0) {
-        da = lane < NT / 32 ? red_s[0][lane] : 0.0;
-        db = lane < NT / 32 ? red_s[1][lane] : 0.0;
-        dc = lane < NT / 32 ? red_s[2][lane] : 0.0;
+        double da = lane < NT / 32 ? red_s[0][lane] : 0.0;
+        double db = lane < NT / 32 ? red_s[1][lane] : 0.0;
+        double dc = lane < NT / 32 ? red_s[2][lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             da += __shfl_down_sync(0xffffffffu, da, o);

@@ -501,6 +501,10 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         nz = (nz + 1) / 2;
     }
     const size_t field = 3 * (size_t)c->lv[0].g.cs;
+    if (field >= (size_t)0x7fffffff) {  // kernels index fields with 32-bit offsets
+        g_create_error = "volume too large for 32-bit field offsets";
+        return fail(DIR_EINVAL);
+    }
     c->total_iters = 0;
     for (int l = 0; l < c->levels; ++l) c->total_iters += p.iters[l];
     const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     const int xc = min(x, g.nx - 1), yc = min(y, g.ny - 1);
     const int xm = max(xc - 1, 0), xp = min(xc + 1, g.nx - 1);
     const int ym = max(yc - 1, 0), yp = min(yc + 1, g.ny - 1);
-    const long long cs = g.cs;
+    const int cs = (int)g.cs;
 
     // W (Eq. 6: W_m + W_s) on the brick plus halo; Eq. 6 also W_m - W_s on the brick
     __shared__ Real Wt[T::GM ? HZ : 1][T::GM ? HY : 1][T::GM ? HX : 1];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
             const int gx = clampi(bx0 + hx - 1, 0, g.nx - 1);
             const int gy = clampi(by0 + hy - 1, 0, g.ny - 1);
             const int gz = clampi(bz0 + hz - 1, 0, g.nz - 1);
-            const long long o = offs(g, gx, gy, gz);
+            const int o = offs(g, gx, gy, gz);
             const Real ux = __ldg(u + o), uy = __ldg(u + o + cs), uz = __ldg(u + o + 2 * cs);
             const Real wm = trilinear(M, g, gx, ux, gy, uy, gz, uz);
             if (T::IC) {
@@ -95,23 +95,23 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
             mcol[k] = __ldg(M + offs(g, xc, yc, clampi(bz0 + k - 1, 0, g.nz - 1)));
     }
 
-    double sd2 = 0.0, sdu = 0.0, su = 0.0;
+    Real sd2 = 0, sdu = 0, su = 0;  // per-thread partial sums
     if (col_valid) {
 #pragma unroll
         for (int k = 0; k < FTZ; ++k) {
             const int z = bz0 + k;
             if (z < g.nz) {
-                const long long o = offs(g, x, y, z);
+                const int o = offs(g, x, y, z);
                 const Real ux = __ldg(u + o), uy = __ldg(u + o + cs), uz = __ldg(u + o + 2 * cs);
                 Real gsx = 0, gsy = 0, gsz = 0, gmx = 0, gmy = 0, gmz = 0, bm = 0, d;
                 if (T::GS) {
-                    const long long ro = offs(g, 0, y, z);
+                    const int ro = offs(g, 0, y, z);
                     gsx = Real(0.5) * (__ldg(S + ro + xp) - __ldg(S + ro + xm));
                     gsy = Real(0.5) * (__ldg(S + offs(g, x, yp, z)) - __ldg(S + offs(g, x, ym, z)));
                     gsz = Real(0.5) * (scol[k + 2] - scol[k]);
                 }
                 if (T::EV) {
-                    const long long ro = offs(g, 0, y, z);
+                    const int ro = offs(g, 0, y, z);
                     const Real mx = Real(0.5) * (__ldg(M + ro + xp) - __ldg(M + ro + xm));
                     const Real my =
                         Real(0.5) * (__ldg(M + offs(g, x, yp, z)) - __ldg(M + offs(g, x, ym, z)));
@@ -135,16 +135,16 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
                 dx = -dx;
                 dy = -dy;
                 dz = -dz;
-                sd2 += (double)(d * d);
-                sdu += (double)r_norm_fast(dx * dx + dy * dy + dz * dz);
-                su += (double)r_norm_fast(ux * ux + uy * uy + uz * uz);
+                sd2 += d * d;
+                sdu += r_norm_fast(dx * dx + dy * dy + dz * dz);
+                su += r_norm_fast(ux * ux + uy * uy + uz * uz);
                 v[o] = ux + dx;
                 v[o + cs] = uy + dy;
                 v[o + 2 * cs] = uz + dz;
             }
         }
     }
-    block_reduce3_atomic<FNT>(sd2, sdu, su, a.red);
+    block_reduce3_atomic<FNT, Real>(sd2, sdu, su, a.red);
 }
 
 template <typename Real>

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
         m_m1 = __ldg(M + offs(g, xc, yc, max(z0 - 1, 0)));
         m_0 = __ldg(M + offs(g, xc, yc, z0));
     }
-    double sd2 = 0.0, sdu = 0.0, su = 0.0;
+    Real sd2 = 0, sdu = 0, su = 0;  // per-thread partial sums
 
     for (int step = 0; step < pipe.nsteps; ++step) {
         if (!pipe.template xpass<FUSED_NT>(&tmap, g, step, tid, w, a.err)) {
@@ -108,12 +108,12 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
             Real m_p1 = 0;
             if (V == 1) m_p1 = __ldg(M + offs(g, xc, yc, zn));
             if (valid) {
-                const long long o = offs(g, x, y, zo);
+                const int o = offs(g, x, y, zo);
                 const Real ux = utile[(0 * STY + fy) * STX + fx];
                 const Real uy = utile[(1 * STY + fy) * STX + fx];
                 const Real uz = utile[(2 * STY + fy) * STX + fx];
                 const Real wv = trilinear(M, g, x, ux, y, uy, zo, uz);
-                const long long ro = offs(g, 0, y, zo);
+                const int ro = offs(g, 0, y, zo);
                 const Real gsx = Real(0.5) * (__ldg(S + ro + xp) - __ldg(S + ro + xm));
                 const Real gsy =
                     Real(0.5) * (__ldg(S + offs(g, x, yp, zo)) - __ldg(S + offs(g, x, ym, zo)));
@@ -133,12 +133,12 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
                 dx = -dx;
                 dy = -dy;
                 dz = -dz;
-                sd2 += (double)(d * d);
-                sdu += (double)r_norm_fast(dx * dx + dy * dy + dz * dz);
-                su += (double)r_norm_fast(ux * ux + uy * uy + uz * uz);
+                sd2 += d * d;
+                sdu += r_norm_fast(dx * dx + dy * dy + dz * dz);
+                su += r_norm_fast(ux * ux + uy * uy + uz * uz);
                 vout[o] = ux + dx;
-                vout[o + g.cs] = uy + dy;
-                vout[o + 2 * g.cs] = uz + dz;
+                vout[o + (int)g.cs] = uy + dy;
+                vout[o + 2 * (int)g.cs] = uz + dz;
             }
             s_m1 = s_0;
             s_0 = s_p1;
@@ -148,14 +148,14 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
             }
         }
     }
-    block_reduce3_atomic<FUSED_NT>(sd2, sdu, su, a.red);
+    block_reduce3_atomic<FUSED_NT, Real>(sd2, sdu, su, a.red);
 }
 
 template <typename Real, int R, int V>
 static cudaError_t launch_rv(const FusedArgs& a, int num_sms, cudaStream_t s) {
     using F = FusedGeom<Real, R>;
     CUtensorMap map;
-    if (!make_plane_map<Real, R, 3>(&map, a.vin, a.g)) return cudaErrorInvalidValue;
+    if (!make_plane_map<Real, R, 3>(&map, a.vin, a.g, 3)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(

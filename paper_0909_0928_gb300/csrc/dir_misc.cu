@@ -33,7 +33,7 @@ __global__ void upsample_kernel(const Real* __restrict__ coarse, Grid3 gc, Real*
     if (x >= gf.nx || y >= gf.ny) return;
     // coarse position x / 2 = (x >> 1) + (x & 1) / 2, exact
     const Real hx = Real(0.5) * (x & 1), hy = Real(0.5) * (y & 1), hz = Real(0.5) * (z & 1);
-    const long long o = offs(gf, x, y, z);
+    const long long o = (long long)offs(gf, x, y, z);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         fine[o + c * gf.cs] =
@@ -46,7 +46,7 @@ __global__ void warp_kernel(const Real* __restrict__ img, const Real* __restrict
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const long long o = offs(g, x, y, z);
+    const long long o = (long long)offs(g, x, y, z);
     const Real w = trilinear(img, g, x, __ldg(u + o), y, __ldg(u + o + g.cs), z,
                              __ldg(u + o + 2 * g.cs));
     out[(long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z)] = (float)w;
@@ -71,7 +71,7 @@ __global__ void ic_invert_kernel(const Real* __restrict__ h, Real* __restrict__ 
         ay = ny_;
         az = nz_;
     }
-    const long long o = offs(g, x, y, z);
+    const long long o = (long long)offs(g, x, y, z);
     u[o] = Real(2) * trilinear(hx, g, x, ax, y, ay, z, az);
     u[o + g.cs] = Real(2) * trilinear(hy, g, x, ax, y, ay, z, az);
     u[o + 2 * g.cs] = Real(2) * trilinear(hz, g, x, ax, y, ay, z, az);
@@ -84,7 +84,7 @@ __global__ void export_kernel(const Real* __restrict__ f, Grid3 g, double sx, do
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long n = (long long)g.nx * g.ny * g.nz;
-    const long long o = offs(g, x, y, z);
+    const long long o = (long long)offs(g, x, y, z);
     const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
     dense[d] = (Out)((Real)sx * f[o]);
     dense[d + n] = (Out)((Real)sy * f[o + g.cs]);
@@ -98,7 +98,7 @@ __global__ void import_kernel(const float* __restrict__ dense, Real* __restrict_
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long n = (long long)g.nx * g.ny * g.nz;
-    const long long o = offs(g, x, y, z);
+    const long long o = (long long)offs(g, x, y, z);
     const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
     for (int c = 0; c < ncomp; ++c) f[o + c * g.cs] = (Real)dense[d + c * n];
 }

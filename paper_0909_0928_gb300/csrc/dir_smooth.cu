@@ -1,10 +1,12 @@
 // dir_smooth.cu -- separable 3-D Gaussian low-pass filter (Sec. 2.5).
 //
 // out = G_sigma * in, applied along x, then y, then z, with replicated edges,
-// on 1 or 3 components: the TMA-fed plane pipeline of dir_stencil.cuh, one
-// thread per (column, component, 4-row group) for the y and z passes.  Every
-// input voxel is read from HBM about once per launch (plus the 2R-plane halo
-// of each z chunk).
+// on 1 or 3 components: the TMA-fed plane pipeline of dir_stencil.cuh.  A
+// block smooths one component of a 32 x 8 column tile over a z chunk, one
+// thread per (column, 4-row group) for the y and z passes, so the three
+// components run as independent blocks (three times the marching chains per
+// SM).  Every input voxel is read from HBM about once per launch (plus the
+// 2R-plane halo of each z chunk).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -14,10 +16,11 @@
 
 namespace dirk {
 
-template <typename Real, int R, int NC>
-__global__ void __launch_bounds__(StencilGeom<Real, R, NC>::YT, (NC == 3 && R <= 4) ? 6 : 1)
+template <typename Real, int R>
+__global__ void __launch_bounds__(StencilGeom<Real, R, 1>::YT)
     smooth_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    constexpr int NC = 1;
     using G = StencilGeom<Real, R, NC>;
     constexpr int K = G::K, NT = G::YT;
     extern __shared__ unsigned char smem_raw[];
@@ -28,16 +31,17 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, NC>::YT, (NC == 3 && R <=
     for (int t = 0; t < K; ++t) w[t] = (Real)a.taps.w[t];
 
     const int tid = threadIdx.x;
-    const int lx = tid % STX;          // y/z role: column, component, row group
-    const int c_own = (tid / STX) % NC;
-    const int q_own = (tid / STX) / NC;
+    const int lx = tid % STX;          // y/z role: column, row group
+    const int q_own = tid / STX;
+    const int comp = blockIdx.z % a.ncomp;
     const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;
     const int x = x0 + lx;
-    const int z0 = blockIdx.z * zchunk;
+    const int z0 = (blockIdx.z / a.ncomp) * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
+    out += (long long)comp * g.cs;
 
     PlanePipe<Real, R, NC> pipe;
-    pipe.setup(smem_raw, g, x0, y0, z0, z1);
+    pipe.setup(smem_raw, g, x0, y0, z0, z1, comp);
     pipe.start(&tmap, g, tid);
 
     Real ring[K][YW];
@@ -48,13 +52,13 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, NC>::YT, (NC == 3 && R <=
 
     for (int step = 0; step < pipe.nsteps; ++step) {
         if (!pipe.template xpass<NT>(&tmap, g, step, tid, w, a.err)) return;
-        pipe.ypass(c_own, q_own, lx, w, ring);
+        pipe.ypass(0, q_own, lx, w, ring);
         if (step >= 2 * R && x < g.nx) {
             const int zo = z0 + step - 2 * R;
 #pragma unroll
             for (int r = 0; r < YW; ++r) {
                 const int y = y0 + q_own * YW + r;
-                if (y < g.ny) out[offs(g, x, y, zo) + c_own * g.cs] = zpass<Real, R>(w, ring, r);
+                if (y < g.ny) out[offs(g, x, y, zo)] = zpass<Real, R>(w, ring, r);
             }
         }
         // no barrier here: the next step's __syncthreads_or orders these reads
@@ -62,30 +66,26 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, NC>::YT, (NC == 3 && R <=
     }
 }
 
-template <typename Real, int R, int NC>
-static cudaError_t launch_rn(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    using G = StencilGeom<Real, R, NC>;
+template <typename Real, int R>
+static cudaError_t launch_r(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    using G = StencilGeom<Real, R, 1>;
     CUtensorMap map;
-    if (!make_plane_map<Real, R, NC>(&map, a.in, a.g)) return cudaErrorInvalidValue;
+    if (!make_plane_map<Real, R, 1>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(
-            smooth_kernel<Real, R, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BASE_SMEM);
+            smooth_kernel<Real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BASE_SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R, NC>, G::YT,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R>, G::YT,
                                                   G::BASE_SMEM);
-    const int zc = stencil_zchunk(a.g, per_sm, num_sms);
-    const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY, (a.g.nz + zc - 1) / zc);
-    smooth_kernel<Real, R, NC><<<grid, dim3(G::YT, 1, 1), G::BASE_SMEM, s>>>(map, a, zc);
+    const int zc = stencil_zchunk(a.g, per_sm, num_sms, a.ncomp);
+    const int chunks = (a.g.nz + zc - 1) / zc;
+    const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY, chunks * a.ncomp);
+    smooth_kernel<Real, R><<<grid, dim3(G::YT, 1, 1), G::BASE_SMEM, s>>>(map, a, zc);
     return cudaGetLastError();
-}
-
-template <typename Real, int R>
-static cudaError_t launch_r(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    return a.ncomp == 3 ? launch_rn<Real, R, 3>(a, num_sms, s) : launch_rn<Real, R, 1>(a, num_sms, s);
 }
 
 template <typename Real>

@@ -81,8 +81,11 @@ struct PlanePipe {
     int z0, nsteps, bx, by;
     bool edge;
 
+    int comp0;  // first component of the copies (tensor-map coordinate 3)
+
     __device__ void setup(unsigned char* smem_raw, const Grid3& g, int x0, int y0, int zstart,
-                          int zend) {
+                          int zend, int c0 = 0) {
+        comp0 = c0;
         base = reinterpret_cast<unsigned char*>(
             (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
         txp = reinterpret_cast<Real*>(base + STAGES * G::SLOT_STRIDE);
@@ -101,7 +104,7 @@ struct PlanePipe {
         const int pc = clampi(z0 - R + step, 0, g.nz - 1);
         fence_proxy_async();
         mbar_arrive_expect_tx(&full[s], (uint32_t)G::SLOT_BYTES);
-        tma_load_4d(base + s * G::SLOT_STRIDE, map, bx, by, pc, 0, &full[s]);
+        tma_load_4d(base + s * G::SLOT_STRIDE, map, bx, by, pc, comp0, &full[s]);
     }
     // thread 0: init barriers and prefetch; everyone: barrier
     __device__ void start(const CUtensorMap* map, const Grid3& g, int tid) {
@@ -224,15 +227,16 @@ inline EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// Tensor map of a pitched (x, y, z, component) array with the plane box of
-// StencilGeom<Real, R, NC>.  Returns false if the driver refuses it.
+// Tensor map of a pitched (x, y, z, component) array of ncomp components with
+// the plane box of StencilGeom<Real, R, NC> (NC components per copy).
+// Returns false if the driver refuses it.
 template <typename Real, int R, int NC>
-inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g) {
+inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
     using G = StencilGeom<Real, R, NC>;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
-                                (cuuint64_t)NC};
+                                (cuuint64_t)ncomp};
     const cuuint64_t strides[3] = {(cuuint64_t)g.px * sizeof(Real),
                                    (cuuint64_t)g.plane * sizeof(Real),
                                    (cuuint64_t)g.cs * sizeof(Real)};
@@ -248,9 +252,10 @@ inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g) {
 // z chunk: as many chunks as fit in one wave of resident blocks (a partial
 // second wave would leave most SMs idle while it runs); short chunks (down to
 // one plane) for small volumes so that enough blocks run
-inline int stencil_zchunk(const Grid3& g, int blocks_per_sm, int num_sms) {
+inline int stencil_zchunk(const Grid3& g, int blocks_per_sm, int num_sms, int copies = 1) {
     if (blocks_per_sm < 1) blocks_per_sm = 1;
-    const long long bxy = (long long)((g.nx + STX - 1) / STX) * ((g.ny + STY - 1) / STY);
+    const long long bxy =
+        (long long)((g.nx + STX - 1) / STX) * ((g.ny + STY - 1) / STY) * copies;
     const long long wave = (long long)blocks_per_sm * num_sms;
     long long chunks = wave / bxy;
     if (chunks < 1) chunks = 1;
