@@ -25,7 +25,16 @@ struct Grid3 {
 struct Taps {
     int R;          // radius: 2R+1 taps
     double w[17];   // w[t + R] for t = -R..R (normalised)
+    float wf[17];   // the same taps rounded for the single-precision path, with
+                    // their exact sum kept at 1 (see make_taps in the engine)
 };
+
+template <typename Real>
+__device__ __forceinline__ Real tap(const Taps& t, int i);
+template <>
+__device__ __forceinline__ float tap<float>(const Taps& t, int i) { return t.wf[i]; }
+template <>
+__device__ __forceinline__ double tap<double>(const Taps& t, int i) { return t.w[i]; }
 
 constexpr int kMaxRadius = 8;
 

@@ -60,8 +60,38 @@ bool make_taps(double sigma, dirk::Taps* t) {
         sum += w[k + R];
     }
     t->R = R;
-    for (int k = 0; k < 17; ++k) t->w[k] = 0.0;
+    for (int k = 0; k < 17; ++k) {
+        t->w[k] = 0.0;
+        t->wf[k] = 0.0f;
+    }
     for (int k = 0; k < 2 * R + 1; ++k) t->w[k] = w[k] / sum;
+    // Single-precision taps: rounding each tap alone leaves their sum off 1 by
+    // a few 1e-8, and every smoothing pass would scale the field by that sum
+    // (3 passes x hundreds of iterations).  Keep the taps symmetric, then move
+    // mirrored pairs (outermost first, finest steps) and finally the centre
+    // tap by one float step at a time while that brings the exact sum closer
+    // to 1.
+    for (int k = 0; k < 2 * R + 1; ++k) t->wf[k] = (float)t->w[k];
+    auto err = [&]() {
+        double s = 0.0;
+        for (int k = 0; k < 2 * R + 1; ++k) s += (double)t->wf[k];
+        return s - 1.0;
+    };
+    for (int pass = 0; pass < 4; ++pass) {
+        for (int k = 0; k <= R; ++k) {
+            const bool centre = (k == R);
+            for (int step = 0; step < 64; ++step) {
+                const double e0 = err();
+                if (e0 == 0.0) break;
+                const float cur = t->wf[k];
+                const float nxt = nextafterf(cur, e0 > 0.0 ? 0.0f : 1.0f);
+                const double delta = ((double)nxt - (double)cur) * (centre ? 1.0 : 2.0);
+                if (fabs(e0 + delta) >= fabs(e0)) break;
+                t->wf[k] = nxt;
+                t->wf[2 * R - k] = nxt;
+            }
+        }
+    }
     return true;
 }
 
@@ -762,3 +792,4 @@ const char* dir_last_error(const dir_ctx* c) { return c ? c->err.c_str() : g_cre
 const char* dir_version(void) { return "gb300-demons 0.2 (sm_103a)"; }
 
 }  // extern "C"
+

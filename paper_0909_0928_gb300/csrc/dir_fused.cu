@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
     Real* __restrict__ vout = static_cast<Real*>(a.v);
     Real w[K];
 #pragma unroll
-    for (int t = 0; t < K; ++t) w[t] = (Real)a.taps.w[t];
+    for (int t = 0; t < K; ++t) w[t] = tap<Real>(a.taps, t);
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * STX, y0 = blockIdx.y * STY;

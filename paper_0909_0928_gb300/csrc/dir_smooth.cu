@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1>::YT)
     Real* __restrict__ out = static_cast<Real*>(a.out);
     Real w[K];
 #pragma unroll
-    for (int t = 0; t < K; ++t) w[t] = (Real)a.taps.w[t];
+    for (int t = 0; t < K; ++t) w[t] = tap<Real>(a.taps, t);
 
     const int tid = threadIdx.x;
     const int lx = tid % STX;          // y/z role: column, row group
