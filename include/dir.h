@@ -88,10 +88,10 @@ typedef struct {
                                     DIR_F32 (default, the production path) or DIR_F64 (the same
                                     kernels in double precision, for verification against an
                                     FP64 reference where the iteration is ill-conditioned) */
-    int fuse;                    /* 1 (default): for Eqs. (1)-(2) without the stop test, fold the
-                                    Gaussian of iteration k into the force pass of iteration k+1
-                                    (same arithmetic, one pass over the field per iteration);
-                                    0: one force and one smoothing launch per iteration */
+    int fuse;                    /* 1: for Eqs. (1)-(2) without the stop test, fold the Gaussian
+                                    of iteration k into the force pass of iteration k+1 (same
+                                    arithmetic, one pass over the field per iteration);
+                                    0 (default): one force and one smoothing launch per iteration */
 } dir_params;
 
 typedef struct {
@@ -183,6 +183,35 @@ int dir_get_history(dir_ctx* ctx, double* out, int max_iters);
  * both device (on_device != 0).
  */
 int dir_warp(dir_ctx* ctx, const void* img_in, void* img_out, dir_dtype dt, int on_device);
+
+/*
+ * Registration that allocates no device memory, for callers that cannot call
+ * cudaMalloc while they run: a host whose memory pool owns the whole device, a
+ * real-time loop or plug-in callback where allocation is forbidden.  The paper
+ * has no counterpart; it is the same pyramid and iterations as dir_create +
+ * dir_register + dir_get_field, with every scratch buffer taken from one
+ * static device array of 48 MiB that the library reserves on each device it is
+ * used on (for as long as the library stays loaded).
+ *   static_img, moving_img  DEVICE pointers, dense float volumes of dims
+ *   dims                    {nx, ny, nz}; the pyramid, two fields and the
+ *                           reduction rows must fit the 48 MiB (about 1.5 M
+ *                           voxels in single precision with 3 levels, e.g.
+ *                           128 x 128 x 90; half that in DIR_F64);
+ *                           larger requests fail with DIR_EINVAL and a message
+ *                           in dir_last_error(NULL), before any device work
+ *   params                  as for dir_create; timing must be 0; use_graph is
+ *                           ignored (kernels are launched directly)
+ *   field_out               DEVICE pointer, 3*N floats: the static-grid field in voxels
+ *   stats_out               NULL, or iterations run and voxel-updates
+ * The first call on a device looks up the array's device address (no
+ * allocation), so make it before capturing the stream into a CUDA graph.  The
+ * work runs on cuda_stream and the call waits for it.  Every call shares the
+ * array: calls whose work could overlap on the GPU (other streams or threads)
+ * race and must be serialised by the caller.
+ */
+int dir_register_noalloc(const float* static_img, const float* moving_img, const int dims[3],
+                         dir_variant variant, const dir_params* params, float* field_out,
+                         void* cuda_stream, dir_stats* stats_out);
 
 /* Frees ctx and everything it owns.  NULL-safe. */
 void dir_destroy(dir_ctx* ctx);

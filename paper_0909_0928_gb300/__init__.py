@@ -33,7 +33,7 @@ VARIANTS = {"passive": 0, "evolved_passive": 1, "active": 2, "double": 3, "adjus
 # every symbol the C header declares
 EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_register_async",
            "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history", "dir_warp", "dir_destroy",
-           "dir_status_string", "dir_last_error", "dir_version"]
+           "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc"]
 
 
 class DirParams(C.Structure):
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_status_string": (C.c_char_p, [ip]),
         "dir_last_error": (C.c_char_p, [vp]),
         "dir_version": (C.c_char_p, []),
+        "dir_register_noalloc": (ip, [vp, vp, C.POINTER(C.c_int * 3), ip, C.POINTER(DirParams),
+                                      vp, vp, C.POINTER(DirStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -231,6 +233,20 @@ def dir_warp(ctx, img_in, img_out, dtype=DIR_F32, on_device=False):
     _check(_lib.dir_warp(ctx, _ptr(img_in, on_device), _ptr(img_out, on_device), int(dtype),
                          int(bool(on_device))), "dir_warp", ctx)
     return img_out
+
+
+def dir_register_noalloc(static_img, moving_img, dims, variant=DIR_PASSIVE,
+                         params: DirParams | None = None, field_out=None, stream=None) -> DirStats:
+    """Registration without device allocation (torch CUDA tensors in and out):
+    scratch comes from the library's static 48 MiB device array."""
+    st = DirStats()
+    d = (C.c_int * 3)(*[int(x) for x in dims])
+    rc = _lib.dir_register_noalloc(_ptr(static_img, True), _ptr(moving_img, True), C.byref(d),
+                                   int(variant), C.byref(params) if params is not None else None,
+                                   _ptr(field_out, True), _stream_handle(stream), C.byref(st))
+    if rc < 0:
+        raise DirError(rc, "dir_register_noalloc", _lib.dir_last_error(None).decode())
+    return st
 
 
 def dir_destroy(ctx):

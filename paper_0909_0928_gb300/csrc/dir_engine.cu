@@ -447,7 +447,7 @@ int dir_params_default(dir_params* p) {
     p->use_graph = 1;
     p->timing = 0;
     p->precision = DIR_F32;
-    p->fuse = 1;
+    p->fuse = 0;
     return DIR_OK;
 }
 
@@ -793,3 +793,179 @@ const char* dir_version(void) { return "gb300-demons 0.2 (sm_103a)"; }
 
 }  // extern "C"
 
+// ------------------------------------------------------------------------
+// Registration without device allocation (see dir_register_noalloc in dir.h).
+//
+// All scratch -- pyramid images, the two field buffers, reduction rows, stop
+// flags -- lives in one file-scope device array.  Its device address is looked
+// up once per device with cudaGetSymbolAddress (the array's name in host code
+// is only a host-side stand-in) and cached.  Every call shares the array, so
+// calls whose GPU work overlaps (different streams, or another host thread)
+// race on it.
+// ------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 48ull << 20;  // 48 MiB
+constexpr int kNoallocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int dir_register_noalloc(const float* static_img, const float* moving_img,
+                                    const int dims[3], dir_variant variant,
+                                    const dir_params* params, float* field_out, void* cuda_stream,
+                                    dir_stats* stats_out) {
+    g_create_error.clear();
+    if (!static_img || !moving_img || !dims || !field_out) return DIR_EINVAL;
+    if ((int)variant < 0 || (int)variant > 5) return DIR_EINVAL;
+    long long nvox = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > DIR_MAX_DIM) return DIR_EINVAL;
+        nvox *= dims[a];
+    }
+    dir_params p;
+    if (params)
+        p = *params;
+    else
+        dir_params_default(&p);
+    const int prc = validate_params(&p);
+    if (prc != DIR_OK) return prc;
+    if (p.timing) return DIR_EINVAL;  // event timing is not offered here
+
+    // the context lives on the stack and points into the static scratch
+    dir_ctx c;
+    for (int a = 0; a < 3; ++a) {
+        c.dims[a] = dims[a];
+        c.spacing[a] = 1.0f;
+    }
+    c.variant = (int)variant;
+    c.p = p;
+    c.p.use_graph = 0;
+    c.fp64 = (p.precision == DIR_F64);
+    c.esz = c.fp64 ? sizeof(double) : sizeof(float);
+    c.stream = (cudaStream_t)cuda_stream;
+    c.levels = p.levels;
+    make_taps(p.sigma, &c.taps);
+    make_taps(1.0, &c.taps1);
+
+    // scratch layout, each piece 256-byte aligned
+    int nx = dims[0], ny = dims[1], nz = dims[2];
+    size_t at = 0;
+    size_t lvl_off[DIR_MAX_LEVELS][2];
+    for (int l = 0; l < c.levels; ++l) {
+        c.lv[l].g = make_grid(nx, ny, nz);
+        lvl_off[l][0] = at;
+        at = align256(at + (size_t)c.lv[l].g.cs * c.esz);
+        lvl_off[l][1] = at;
+        at = align256(at + (size_t)c.lv[l].g.cs * c.esz);
+        nx = (nx + 1) / 2;
+        ny = (ny + 1) / 2;
+        nz = (nz + 1) / 2;
+    }
+    const size_t field = 3 * (size_t)c.lv[0].g.cs;
+    if (field >= (size_t)0x7fffffff) return DIR_EINVAL;
+    c.total_iters = 0;
+    for (int l = 0; l < c.levels; ++l) c.total_iters += p.iters[l];
+    const size_t nred = (size_t)(c.total_iters > 0 ? c.total_iters : 1);
+    const size_t offA = at;
+    at = align256(at + field * c.esz);
+    const size_t offB = at;
+    at = align256(at + field * c.esz);
+    const size_t offRed = at;
+    at = align256(at + 3 * nred * sizeof(double));
+    const size_t offL = at;
+    at = align256(at + nred * sizeof(double));
+    const size_t offCtl = at;
+    at = align256(at + DIR_MAX_LEVELS * sizeof(int));
+    const size_t offErr = at;
+    at = align256(at + sizeof(int));
+    if (at > kNoallocScratchBytes) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "dir_register_noalloc: this volume and schedule need %.1f MiB of scratch, "
+                 "the static limit is %.0f MiB",
+                 at / 1048576.0, kNoallocScratchBytes / 1048576.0);
+        g_create_error = buf;
+        return DIR_EINVAL;
+    }
+
+    // device address of the static scratch, once per device, that device current
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        g_create_error = "dir_register_noalloc: no usable current device";
+        return DIR_ECUDA;
+    }
+    char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess || !ptr) {
+                set_err(nullptr, "cudaGetSymbolAddress", e);
+                return DIR_ECUDA;
+            }
+            g_noalloc_ptr[dev] = ptr;
+        }
+        base = static_cast<char*>(g_noalloc_ptr[dev]);
+    }
+    c.device = dev;
+    e = cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "cudaDeviceGetAttribute", e);
+        return DIR_ECUDA;
+    }
+    for (int l = 0; l < c.levels; ++l) {
+        c.lv[l].S = base + lvl_off[l][0];
+        c.lv[l].M = base + lvl_off[l][1];
+    }
+    c.A = base + offA;
+    c.B = base + offB;
+    c.red = reinterpret_cast<double*>(base + offRed);
+    c.lhist = reinterpret_cast<double*>(base + offL);
+    c.ctl = reinterpret_cast<int*>(base + offCtl);
+    c.derr = reinterpret_cast<int*>(base + offErr);
+
+    int rc = upload_pair(&c, static_img, moving_img, 1, c.stream);
+    if (rc == DIR_OK) rc = enqueue_registration(&c, c.stream, false);
+    if (rc == DIR_OK && dirk::launch_export_field(c.fp64, c.final_field, c.lv[0].g, 1.0, 1.0, 1.0,
+                                                  field_out, false, c.stream) != cudaSuccess)
+        rc = DIR_ECUDA;
+    int ctl[DIR_MAX_LEVELS + 1] = {0};
+    if (rc == DIR_OK &&
+        (cudaMemcpyAsync(ctl, c.ctl, c.levels * sizeof(int), cudaMemcpyDeviceToHost, c.stream) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(ctl + DIR_MAX_LEVELS, c.derr, sizeof(int), cudaMemcpyDeviceToHost,
+                         c.stream) != cudaSuccess ||
+         cudaStreamSynchronize(c.stream) != cudaSuccess))
+        rc = DIR_ECUDA;
+    if (rc != DIR_OK) {
+        if (!c.err.empty()) g_create_error = c.err;
+        return rc;
+    }
+    if (ctl[DIR_MAX_LEVELS] != 0) return DIR_ETIMEOUT;
+    if (stats_out) {
+        memset(stats_out, 0, sizeof *stats_out);
+        stats_out->levels = c.levels;
+        long long vu = 0;
+        for (int lc = 0; lc < c.levels; ++lc) {
+            int run = p.iters[lc];
+            if (ctl[lc] != kStopUnset && ctl[lc] + 1 < run) run = ctl[lc] + 1;
+            stats_out->iters_run[lc] = run;
+            const Grid3& g = c.lv[c.levels - 1 - lc].g;
+            vu += (long long)g.nx * g.ny * g.nz * run;
+        }
+        stats_out->voxel_updates = vu;
+        stats_out->kernel_launches = c.launches + 1;
+    }
+    return DIR_OK;
+}
