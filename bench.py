@@ -317,8 +317,8 @@ def main():
     per_variant = None
     if not args.no_variants:
         per_variant = {}
-        for vid, alpha, fuse in ((0, 0.4, 1), (0, 0.4, 0), (1, 0.4, 1), (2, 0.4, 1), (3, 0.4, 1),
-                                 (4, 0.4, 1), (4, 2.0, 1), (5, 0.4, 1)):
+        for vid, alpha, fuse in ((0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 0), (2, 0.4, 0), (3, 0.4, 0),
+                                 (4, 0.4, 0), (4, 2.0, 0), (5, 0.4, 0)):
             p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, fuse=fuse)
             c2 = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, vid, p2, stream)
             ms = []
@@ -329,7 +329,7 @@ def main():
                     ms.append(st.ms_total)
             dl.dir_destroy(c2)
             name = VARIANT_NAMES[vid] + (f"_alpha{alpha}" if vid == 4 else "") + \
-                ("" if fuse or vid > 1 else "_unfused")
+                ("_fused" if fuse else "")
             med = statistics.median(ms)
             per_variant[name] = {"ms_p50": med, "voxel_updates_per_s": vu_step / (med / 1e3)}
 

@@ -337,7 +337,8 @@ OR_EXPORT void or_force_arrays(int variant, double alpha, const double* d, const
 static struct {
     double rel;
     uint64_t key;
-} probe_now = {0.0, 0};
+    int coherent;
+} probe_now = {0.0, 0, 0};
 
 static uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -347,6 +348,10 @@ static uint64_t mix64(uint64_t z) {
 
 static void probe_perturb(double* a, size_t n, uint64_t which) {
     if (probe_now.rel == 0.0) return;
+    if (probe_now.coherent) {  /* the same relative nudge everywhere */
+        for (size_t c = 0; c < n; ++c) a[c] *= 1.0 + probe_now.rel;
+        return;
+    }
     const uint64_t base = mix64(probe_now.key ^ (which * 0xD1B54A32D192ED03ull));
     for (size_t c = 0; c < n; ++c) {
         const uint64_t z = mix64(base + (uint64_t)(c + 1) * 0x9E3779B97F4A7C15ull);
@@ -494,7 +499,9 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /*                xi), xi uniform in [-1, 1) from a counter-based hash keyed  */
 /*                by probe_seed; probe_rel = 2^-24 models float rounding,     */
 /*                2^-53 double rounding                                       */
-/*   probe_seed   key of the probe's hash                                     */
+/*   probe_seed   key of the probe's hash; 0 makes the probe coherent: every   */
+/*                value is scaled by (1 + probe_rel), the spatially correlated  */
+/*                kind of rounding a smooth field undergoes                     */
 /* Returns 0 or a negative code.                                              */
 /* ------------------------------------------------------------------------- */
 OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, int nz,
@@ -586,6 +593,7 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
         for (int it = 0; it < iters[lc]; ++it) {
             double red[3];
             probe_now.rel = probe_rel;
+            probe_now.coherent = (probe_seed == 0);
             probe_now.key = probe_seed * 0x9E3779B97F4A7C15ull + (uint64_t)stat_at + 1;
             rc = or_iterate(variant, alpha, sigma, Sl[l], Ml[l], gsx, gsy, gsz,
                             variant == OR_EVOLVED_PASSIVE ? bm : NULL, ux, uy, uz, cx, cy, cz,
