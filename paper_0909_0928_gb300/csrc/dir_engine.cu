@@ -164,9 +164,12 @@ static void set_err(dir_ctx* c, const char* what, cudaError_t e) {
         }                                   \
     } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// context's stream): freeing a finished context does not synchronise the
+// device, so other contexts keep running (the serving loop relies on it).
 static int ensure(dir_ctx* c, void** p, size_t bytes) {
     if (*p) return DIR_OK;
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(p, bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         c->err = "device allocation failed";
@@ -270,6 +273,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.g = g;
         fa.alpha2 = c->p.alpha * c->p.alpha;
         fa.stop_iter = c->ctl + lc;
+        fa.depth = dirk::force_brick_depth(g, c->num_sms, 4);
         dirk::SmoothArgs sa;
         sa.g = g;
         sa.ncomp = 3;
@@ -399,16 +403,10 @@ static void release(dir_ctx* c) {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap) cudaStreamDestroy(c->cap);
-    cudaFree(c->img_pool);
-    cudaFree(c->A);
-    cudaFree(c->B);
-    cudaFree(c->red);
-    cudaFree(c->lhist);
-    cudaFree(c->ctl);
-    cudaFree(c->derr);
-    cudaFree(c->stage_img);
-    cudaFree(c->stage_f32);
-    cudaFree(c->stage_f64);
+    void* bufs[] = {c->img_pool, c->A, c->B, c->red, c->lhist, c->ctl, c->derr,
+                    c->stage_img, c->stage_f32, c->stage_f64};
+    for (void* b : bufs)
+        if (b) cudaFreeAsync(b, c->stream);
     delete c;
 }
 
@@ -538,13 +536,14 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
     c->total_iters = 0;
     for (int l = 0; l < c->levels; ++l) c->total_iters += p.iters[l];
     const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
-    if (cudaMalloc(&c->img_pool, pool * c->esz) != cudaSuccess ||
-        cudaMalloc(&c->A, field * c->esz) != cudaSuccess ||
-        cudaMalloc(&c->B, field * c->esz) != cudaSuccess ||
-        cudaMalloc(&c->red, 3 * nred * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->lhist, nred * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->ctl, DIR_MAX_LEVELS * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess) {
+    cudaStream_t st = c->stream;
+    if (cudaMallocAsync(&c->img_pool, pool * c->esz, st) != cudaSuccess ||
+        cudaMallocAsync(&c->A, field * c->esz, st) != cudaSuccess ||
+        cudaMallocAsync(&c->B, field * c->esz, st) != cudaSuccess ||
+        cudaMallocAsync(&c->red, 3 * nred * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&c->lhist, nred * sizeof(double), st) != cudaSuccess ||
+        cudaMallocAsync(&c->ctl, DIR_MAX_LEVELS * sizeof(int), st) != cudaSuccess ||
+        cudaMallocAsync(&c->derr, sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "device allocation failed";
         return fail(DIR_ENOMEM);

@@ -9,8 +9,9 @@
 //   v     = u - dr                         total field, smoothed afterwards
 //   red  += {sum d^2, sum |du|, sum |u|}   FP64 atomics, one per block
 //
-// A block of 32 x 8 threads owns a 32 x 8 x ZT brick; each thread handles the
-// ZT voxels of its (x, y) column.  Loads of different voxels are independent,
+// A block of 32 x 8 threads owns a 32 x 8 x FTZ brick; each thread handles the
+// FTZ voxels of its (x, y) column (FTZ = 8 for large levels, down to 1 for
+// small ones so that enough blocks run).  Loads of different voxels are independent,
 // so many are in flight per warp.  The static gradient uses the thread's
 // column of S in registers plus x/y neighbours through L1.  Variants that need
 // the gradient of the warped image (Eqs. 3-6) first compute W on the brick
@@ -24,8 +25,8 @@
 
 namespace dirk {
 
-constexpr int FTX = 32, FTY = 8, FNT = FTX * FTY, FTZ = 8;
-constexpr int HX = FTX + 2, HY = FTY + 2, HZ = FTZ + 2;
+constexpr int FTX = 32, FTY = 8, FNT = FTX * FTY;
+constexpr int HX = FTX + 2, HY = FTY + 2;
 
 template <int V>
 struct VT {
@@ -35,8 +36,9 @@ struct VT {
     static constexpr bool EV = (V == 1);
 };
 
-template <typename Real, int V>
+template <typename Real, int V, int FTZ>
 __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
+    constexpr int HZ = FTZ + 2;
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;  // uniform across the grid
     using T = VT<V>;
     const Grid3 g = a.g;
@@ -147,20 +149,41 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     block_reduce3_atomic<FNT, Real>(sd2, sdu, su, a.red);
 }
 
-template <typename Real>
-static cudaError_t launch_t(int variant, const ForceArgs& a, cudaStream_t s) {
+template <typename Real, int FTZ>
+static cudaError_t launch_z(int variant, const ForceArgs& a, cudaStream_t s) {
     const dim3 block(FTX, FTY, 1);
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
     switch (variant) {
-        case 0: force_kernel<Real, 0><<<grid, block, 0, s>>>(a); break;
-        case 1: force_kernel<Real, 1><<<grid, block, 0, s>>>(a); break;
-        case 2: force_kernel<Real, 2><<<grid, block, 0, s>>>(a); break;
-        case 3: force_kernel<Real, 3><<<grid, block, 0, s>>>(a); break;
-        case 4: force_kernel<Real, 4><<<grid, block, 0, s>>>(a); break;
-        case 5: force_kernel<Real, 5><<<grid, block, 0, s>>>(a); break;
+        case 0: force_kernel<Real, 0, FTZ><<<grid, block, 0, s>>>(a); break;
+        case 1: force_kernel<Real, 1, FTZ><<<grid, block, 0, s>>>(a); break;
+        case 2: force_kernel<Real, 2, FTZ><<<grid, block, 0, s>>>(a); break;
+        case 3: force_kernel<Real, 3, FTZ><<<grid, block, 0, s>>>(a); break;
+        case 4: force_kernel<Real, 4, FTZ><<<grid, block, 0, s>>>(a); break;
+        case 5: force_kernel<Real, 5, FTZ><<<grid, block, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Brick depth: the deepest of 8, 4, 2, 1 that still gives at least `waves`
+// waves of resident blocks (4 per SM), so small levels spread over the GPU.
+int force_brick_depth(const Grid3& g, int num_sms, int waves) {
+    const long long bxy = (long long)((g.nx + FTX - 1) / FTX) * ((g.ny + FTY - 1) / FTY);
+    const long long want = (long long)waves * 4 * num_sms;
+    for (int d = 8; d > 1; d /= 2)
+        if (bxy * ((g.nz + d - 1) / d) >= want) return d;
+    return 1;
+}
+
+template <typename Real>
+static cudaError_t launch_t(int variant, const ForceArgs& a, cudaStream_t s) {
+    switch (a.depth) {
+        case 8: return launch_z<Real, 8>(variant, a, s);
+        case 4: return launch_z<Real, 4>(variant, a, s);
+        case 2: return launch_z<Real, 2>(variant, a, s);
+        case 1: return launch_z<Real, 1>(variant, a, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s) {

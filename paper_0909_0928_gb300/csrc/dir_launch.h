@@ -23,8 +23,10 @@ struct ForceArgs {
     double* red;         // 3 doubles, accumulated with atomics
     const int* stop_iter;
     int iter;
+    int depth;           // voxels per thread along z: 1, 2, 4 or 8
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
+int force_brick_depth(const Grid3& g, int num_sms, int waves);
 
 // Separable Gaussian (Sec. 2.5 low-pass filter), x then y then z, replicate
 // edges, ncomp components cs apart, fed by TMA.  Skips when *stop_iter < iter.

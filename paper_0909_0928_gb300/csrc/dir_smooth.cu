@@ -17,11 +17,11 @@
 namespace dirk {
 
 template <typename Real, int R>
-__global__ void __launch_bounds__(StencilGeom<Real, R, 1>::YT)
+__global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8>::YT)
     smooth_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
     constexpr int NC = 1;
-    using G = StencilGeom<Real, R, NC>;
+    using G = StencilGeom<Real, R, NC, 8>;
     constexpr int K = G::K, NT = G::YT;
     extern __shared__ unsigned char smem_raw[];
     const Grid3 g = a.g;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1>::YT)
     const int z1 = min(z0 + zchunk, g.nz);
     out += (long long)comp * g.cs;
 
-    PlanePipe<Real, R, NC> pipe;
+    PlanePipe<Real, R, NC, 8> pipe;
     pipe.setup(smem_raw, g, x0, y0, z0, z1, comp);
     pipe.start(&tmap, g, tid);
 
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1>::YT)
 
 template <typename Real, int R>
 static cudaError_t launch_r(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    using G = StencilGeom<Real, R, 1>;
+    using G = StencilGeom<Real, R, 1, 8>;
     CUtensorMap map;
     if (!make_plane_map<Real, R, 1>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation

@@ -19,7 +19,7 @@
 
 namespace dirk {
 
-constexpr int STX = 32, STY = 8, STAGES = 4, YW = 4;
+constexpr int STX = 32, STY = 8, YW = 4;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 template <typename Real>
@@ -53,8 +53,9 @@ __device__ __forceinline__ void store4(double* dst, const double* s) {
     reinterpret_cast<double2*>(dst)[1] = make_double2(s[2], s[3]);
 }
 
-template <typename Real, int R, int NC>
+template <typename Real, int R, int NC, int STAGES_ = 4>
 struct StencilGeom {
+    static constexpr int STAGES = STAGES_;
     static constexpr int HA = (R + 3) / 4 * 4;   // x halo rounded up: TMA x start 16-byte aligned
     static constexpr int WB = STX + 2 * HA;      // box width
     static constexpr int H = STY + 2 * R;        // box height
@@ -72,9 +73,10 @@ struct StencilGeom {
 };
 
 // Per-block state of the TMA plane pipeline.
-template <typename Real, int R, int NC>
+template <typename Real, int R, int NC, int STAGES_ = 4>
 struct PlanePipe {
-    using G = StencilGeom<Real, R, NC>;
+    using G = StencilGeom<Real, R, NC, STAGES_>;
+    static constexpr int STAGES = STAGES_;
     unsigned char* base;
     Real* txp;
     uint64_t* full;
@@ -232,7 +234,7 @@ inline EncodeTiledFn encode_fn() {
 // Returns false if the driver refuses it.
 template <typename Real, int R, int NC>
 inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
-    using G = StencilGeom<Real, R, NC>;
+    using G = StencilGeom<Real, R, NC>;  // the box does not depend on the stage count
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
