@@ -9,6 +9,7 @@ second of device time) with s per registration p50/p99 beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--variant passive]
   python bench.py --impl reference   # FP64 CPU oracle on the host cores
+  python bench.py --form batch       # 32 uneven int16 pairs: one graph vs 32 plain runs
 
 Prints one JSON line on rank 0.
 """
@@ -186,6 +187,114 @@ def run_reference(args):
     return 0
 
 
+BATCH_PAIRS = 32
+
+
+def batch_pairs(n=BATCH_PAIRS, seed=3):
+    """Uneven int16 pairs cropped from one seeded 256 x 256 x 128 lung phantom
+    (RBF motion up to 12 mm, 20% compression of the lower lung): sizes uniform
+    in 96..256 x 96..256 x 48..128, passive or inverse-consistent at random."""
+    import numpy as np
+    from phantom import PhantomSpec, SplitMix64Stream, make_lung_phantom
+    ph = make_lung_phantom(PhantomSpec(dims=(256, 256, 128), spacing=SPACING, seed=seed,
+                                       a_max_mm=12.0, compression=0.2,
+                                       compression_region="lower", n_landmarks=10))
+    S = np.round(ph["S"]).astype(np.int16)
+    M = np.round(ph["M"]).astype(np.int16)
+    rng = SplitMix64Stream(seed, sid=21)
+    out = []
+    for _ in range(n):
+        r = rng.uniform(7)
+        nx, ny = 96 + int(r[0] * 161), 96 + int(r[1] * 161)
+        nz = 48 + int(r[2] * 81)
+        x0, y0 = int(r[3] * (257 - nx)), int(r[4] * (257 - ny))
+        z0 = int(r[5] * (129 - nz))
+        sl = (slice(z0, z0 + nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
+        out.append((np.ascontiguousarray(S[sl]), np.ascontiguousarray(M[sl]),
+                    0 if r[6] < 0.5 else 5))
+    return out
+
+
+def run_batch(args):
+    """Batched form against the plain per-pair form on the same 32 contexts."""
+    import numpy as np
+    import torch
+    import paper_0909_0928_gb300 as dl
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    pairs = batch_pairs()
+    ctxs, dev, vu = [], [], 0
+    for S, M, v in pairs:
+        nz, ny, nx = S.shape
+        St, Mt = torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda()
+        dev.append((St, Mt))
+        p = dl.dir_params_default(levels=LEVELS, iters=ITERS)
+        ctxs.append(dl.dir_create(St, Mt, (nx, ny, nz), SPACING, dl.DIR_I16, True, v, p, stream))
+        vu += voxel_updates((nx, ny, nz), LEVELS, ITERS)
+    n = len(ctxs)
+
+    def sequential(reps):
+        done = []   # completion time of each pair after the start of its round
+        t_all = 0.0
+        for _ in range(reps):
+            t = 0.0
+            for c in ctxs:
+                t += dl.dir_register(c).ms_total
+                done.append(t)
+            t_all += t
+        return t_all / reps, done
+
+    sequential(1)
+    plain_ms, plain_done = sequential(args.steps)
+    ref = []
+    for (S, _, _), c in zip(pairs, ctxs):
+        f = np.empty((3,) + S.shape, np.float32)
+        dl.dir_get_field(c, f)
+        ref.append(f)
+    t0 = time.perf_counter()
+    shapes = [dl.dir_autotune(c, reps=3, levels=LEVELS) for c in ctxs]
+    tune_s = time.perf_counter() - t0
+    sequential(1)
+    tuned_ms, _ = sequential(args.steps)
+    best = None
+    per_branches = {}
+    for br in (4, 8, 16, 32):
+        b = dl.dir_batch_create(ctxs, branches=br, stream=stream)
+        for _ in range(args.warmup):
+            dl.dir_batch_run(b)
+        ms = statistics.median([dl.dir_batch_run(b) for _ in range(args.steps)])
+        per_branches[br] = ms
+        if best is None or ms < per_branches[best]:
+            best = br
+        dl.dir_batch_destroy(b)
+    same = True
+    for (S, _, _), c, f0 in zip(pairs, ctxs, ref):
+        f = np.empty((3,) + S.shape, np.float32)
+        dl.dir_get_field(c, f)
+        same = same and bool(np.array_equal(f, f0))
+    for c in ctxs:
+        dl.dir_destroy(c)
+    bms = per_branches[best]
+    q = lambda xs, p: float(np.quantile(np.asarray(xs), p))
+    line = {"mode": "batch", "pairs": n, "variants": {"passive": sum(v == 0 for *_, v in pairs),
+                                                      "inverse_consistent": sum(v == 5 for *_, v in pairs)},
+            "sizes": "96..256 x 96..256 x 48..128 int16 HU crops, FP32 fields, 3 levels 200/100/50",
+            "voxel_updates": vu,
+            "plain_sequential": {"ms": plain_ms, "volumes_per_s": n / (plain_ms / 1e3),
+                                 "voxel_updates_per_s": vu / (plain_ms / 1e3),
+                                 "completion_p50_ms": q(plain_done, 0.5),
+                                 "completion_p99_ms": q(plain_done, 0.99)},
+            "tuned_sequential": {"ms": tuned_ms, "volumes_per_s": n / (tuned_ms / 1e3)},
+            "batched": {"ms": bms, "branches": best, "volumes_per_s": n / (bms / 1e3),
+                        "voxel_updates_per_s": vu / (bms / 1e3),
+                        "completion_p50_ms": bms, "completion_p99_ms": bms,
+                        "per_branch_count_ms": per_branches},
+            "speedup_vs_plain": plain_ms / bms, "fields_identical": same,
+            "autotune_s": tune_s, "tuned_shapes_first_pair": shapes[0]}
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,12 +305,15 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--form", default="plain", choices=["plain", "batch"])
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batch":
+        return run_batch(args)
 
     import numpy as np
     import torch

@@ -185,6 +185,35 @@ int dir_get_history(dir_ctx* ctx, double* out, int max_iters);
 int dir_warp(dir_ctx* ctx, const void* img_in, void* img_out, dir_dtype dt, int on_device);
 
 /*
+ * Batched registration: one CUDA graph that runs the registrations of n
+ * contexts (each created with dir_create, params.timing 0, none pending),
+ * spread over `branches` concurrent branches (longest job first onto the least
+ * loaded branch), replayed by one graph launch on cuda_stream.  Small volumes
+ * and coarse pyramid levels, each too small to fill the GPU alone, run
+ * together.  The contexts stay owned by the caller and must outlive the batch;
+ * after dir_batch_run each context's field, history and warp are available as
+ * after dir_register.  dir_batch_run waits for the batch and reports its
+ * device time in *ms_out (may be NULL).  Multi-job batching of this kind is
+ * beyond the paper, which registers one pair at a time.
+ */
+typedef struct dir_batch dir_batch;
+int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, int branches,
+                     void* cuda_stream);
+int dir_batch_run(dir_batch* batch, float* ms_out);
+void dir_batch_destroy(dir_batch* batch);  /* NULL-safe */
+
+/*
+ * Launch-shape autotuning for one context, after a finished dir_register:
+ * for each pyramid level, times the force kernel with 1, 2, 4 and 8 voxels
+ * per thread along z and the smoothing kernel with several z chunks
+ * (`reps` launches each), keeps the fastest of each for the context's later
+ * registrations (and batches built afterwards), and writes them to
+ * shapes_out[2*l], shapes_out[2*l+1] for level l (finest = 0) if not NULL.
+ * The registered field is kept.
+ */
+int dir_autotune(dir_ctx* ctx, int reps, int* shapes_out);
+
+/*
  * Registration that allocates no device memory, for callers that cannot call
  * cudaMalloc while they run: a host whose memory pool owns the whole device, a
  * real-time loop or plug-in callback where allocation is forbidden.  The paper

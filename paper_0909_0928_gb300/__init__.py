@@ -33,7 +33,8 @@ VARIANTS = {"passive": 0, "evolved_passive": 1, "active": 2, "double": 3, "adjus
 # every symbol the C header declares
 EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_register_async",
            "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history", "dir_warp", "dir_destroy",
-           "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc"]
+           "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc",
+           "dir_batch_create", "dir_batch_run", "dir_batch_destroy", "dir_autotune"]
 
 
 class DirParams(C.Structure):
@@ -94,6 +95,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_version": (C.c_char_p, []),
         "dir_register_noalloc": (ip, [vp, vp, C.POINTER(C.c_int * 3), ip, C.POINTER(DirParams),
                                       vp, vp, C.POINTER(DirStats)]),
+        "dir_batch_create": (ip, [C.POINTER(vp), C.POINTER(vp), ip, ip, vp]),
+        "dir_batch_run": (ip, [vp, C.POINTER(C.c_float)]),
+        "dir_batch_destroy": (None, [vp]),
+        "dir_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,7 +142,8 @@ def _stream_handle(stream) -> C.c_void_p:
 
 def _check(code: int, where: str, ctx=None):
     if code < 0:
-        detail = _lib.dir_last_error(ctx).decode() if ctx is not None or where == "dir_create" else ""
+        glob = where in ("dir_create", "dir_batch_create", "dir_batch_run")
+        detail = _lib.dir_last_error(ctx).decode() if ctx is not None or glob else ""
         raise DirError(code, where, detail)
     return code
 
@@ -252,6 +258,36 @@ def dir_register_noalloc(static_img, moving_img, dims, variant=DIR_PASSIVE,
 def dir_destroy(ctx):
     if ctx is not None:
         _lib.dir_destroy(ctx)
+
+
+def dir_batch_create(ctxs, branches: int = 8, stream=None):
+    """One captured CUDA graph that runs the registrations of `ctxs` (contexts
+    from dir_create) on `branches` concurrent branches."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    out = C.c_void_p()
+    _check(_lib.dir_batch_create(C.byref(out), arr, len(ctxs), int(branches),
+                                 _stream_handle(stream)), "dir_batch_create")
+    return out
+
+
+def dir_batch_run(batch) -> float:
+    """Replay the batch and wait for it; returns its device time in ms."""
+    ms = C.c_float()
+    _check(_lib.dir_batch_run(batch, C.byref(ms)), "dir_batch_run")
+    return float(ms.value)
+
+
+def dir_batch_destroy(batch):
+    if batch is not None:
+        _lib.dir_batch_destroy(batch)
+
+
+def dir_autotune(ctx, reps: int = 5, levels: int = DIR_MAX_LEVELS) -> list:
+    """Pick per-level force brick depths and smoothing z chunks by timing them;
+    returns [(depth, zchunk)] per level, finest first (zchunk 0 = one wave)."""
+    shapes = (C.c_int * (2 * DIR_MAX_LEVELS))()
+    _check(_lib.dir_autotune(ctx, int(reps), shapes), "dir_autotune", ctx)
+    return [(shapes[2 * l], shapes[2 * l + 1]) for l in range(levels)]
 
 
 # --------------------------------------------------------------- convenience

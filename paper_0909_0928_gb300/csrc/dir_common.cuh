@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,6 +63,25 @@ __device__ __forceinline__ float r_norm_fast(float s) { return s > 0.0f ? s * rs
 __device__ __forceinline__ double r_norm_fast(double s) { return sqrt(s); }
 __device__ __forceinline__ double r_clamp(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
 
+// ---------------------------------------------------------------- storage types
+// Images and fields may be stored narrower than the arithmetic: int16 HU
+// images (exact), bf16 fields.  Every load widens to Real, every store rounds
+// to the storage type (round to nearest even).
+typedef __nv_bfloat16 bf16;
+
+template <typename Real, typename T>
+__device__ __forceinline__ Real ldg_as(const T* p) { return (Real)__ldg(p); }
+template <>
+__device__ __forceinline__ float ldg_as<float, bf16>(const bf16* p) { return __bfloat162float(__ldg(p)); }
+template <typename Real, typename T>
+__device__ __forceinline__ Real ld_as(const T* p) { return (Real)*p; }
+template <>
+__device__ __forceinline__ float ld_as<float, bf16>(const bf16* p) { return __bfloat162float(*p); }
+template <typename T, typename Real>
+__device__ __forceinline__ T st_as(Real v) { return (T)v; }
+template <>
+__device__ __forceinline__ bf16 st_as<bf16, float>(float v) { return __float2bfloat16_rn(v); }
+
 // One axis of the trilinear setup (Sec. 2.5 interpolation, clamped
 // coordinates) at p = base + off, base an integer voxel index: clamp p to
 // [0, n-1], lower corner floor(p) kept <= n-2 so the upper corner exists,
@@ -91,24 +111,32 @@ __device__ __forceinline__ void axis_setup(int base, Real off, int n, int& i0, i
 }
 
 // Software trilinear interpolation of a pitched volume at the continuous voxel
-// position (bx + ox, by + oy, bz + oz); lerps along x, then y, then z.
-template <typename Real>
-__device__ __forceinline__ Real trilinear(const Real* __restrict__ I, const Grid3& g, int bx,
-                                          Real ox, int by, Real oy, int bz, Real oz) {
+// position (bx + ox, by + oy, bz + oz), minus a reference value `ref`; lerps
+// along x, then y, then z.  The corners are taken relative to ref before the
+// lerps, so the result is rounded to the precision of its own size rather
+// than of the image's: with ref = S(x), M(x + u) - S(x) has single-precision
+// error of a few ulp of the intensity difference, where interpolating M first
+// would leave an error of an ulp of |M| (about 6e-5 HU at -1000 HU), which the
+// demons iteration amplifies in homogeneous regions.  Each corner difference
+// is exact when the corner is within a factor two of ref.
+template <typename Real, typename T>
+__device__ __forceinline__ Real trilinear(const T* __restrict__ I, const Grid3& g, int bx,
+                                          Real ox, int by, Real oy, int bz, Real oz,
+                                          Real ref = Real(0)) {
     int x0, x1, y0, y1, z0, z1;
     Real fx, fy, fz;
     axis_setup(bx, ox, g.nx, x0, x1, fx);
     axis_setup(by, oy, g.ny, y0, y1, fy);
     axis_setup(bz, oz, g.nz, z0, z1, fz);
     const int pl = (int)g.plane;
-    const Real* p00 = I + (g.px * y0 + pl * z0);
-    const Real* p10 = I + (g.px * y1 + pl * z0);
-    const Real* p01 = I + (g.px * y0 + pl * z1);
-    const Real* p11 = I + (g.px * y1 + pl * z1);
-    const Real c000 = __ldg(p00 + x0), c100 = __ldg(p00 + x1);
-    const Real c010 = __ldg(p10 + x0), c110 = __ldg(p10 + x1);
-    const Real c001 = __ldg(p01 + x0), c101 = __ldg(p01 + x1);
-    const Real c011 = __ldg(p11 + x0), c111 = __ldg(p11 + x1);
+    const T* p00 = I + (g.px * y0 + pl * z0);
+    const T* p10 = I + (g.px * y1 + pl * z0);
+    const T* p01 = I + (g.px * y0 + pl * z1);
+    const T* p11 = I + (g.px * y1 + pl * z1);
+    const Real c000 = ldg_as<Real>(p00 + x0) - ref, c100 = ldg_as<Real>(p00 + x1) - ref;
+    const Real c010 = ldg_as<Real>(p10 + x0) - ref, c110 = ldg_as<Real>(p10 + x1) - ref;
+    const Real c001 = ldg_as<Real>(p01 + x0) - ref, c101 = ldg_as<Real>(p01 + x1) - ref;
+    const Real c011 = ldg_as<Real>(p11 + x0) - ref, c111 = ldg_as<Real>(p11 + x1) - ref;
     const Real gx = Real(1) - fx, gy = Real(1) - fy, gz = Real(1) - fz;
     const Real v00 = c000 * gx + c100 * fx;
     const Real v10 = c010 * gx + c110 * fx;

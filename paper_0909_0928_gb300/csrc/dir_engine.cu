@@ -109,7 +109,16 @@ struct dir_ctx {
     int variant;
     dir_params p;
     bool fp64;
-    size_t esz;
+    size_t esz;          // arithmetic type (float or double) = coarse image storage
+    int real_type;       // kStoreF32 or kStoreF64
+    int img0_type;       // storage of the finest-level images (kStoreI16 for int16 HU input)
+    size_t iesz0;        // its element size
+    int field_type;      // storage of the fields (kStoreF32, kStoreBF16, kStoreF64)
+    size_t fesz;         // its element size
+    int input_dtype;     // dir_dtype of the images the caller passes (DIR_F32 or DIR_I16)
+
+    int img_type(int l) const { return l == 0 ? img0_type : real_type; }
+    size_t img_esz(int l) const { return l == 0 ? iesz0 : esz; }
     cudaStream_t stream;
     int device;
     int num_sms;
@@ -125,6 +134,8 @@ struct dir_ctx {
     int total_iters = 0;
     int level_first[DIR_MAX_LEVELS];
     int fused_level[DIR_MAX_LEVELS];
+    int tune_depth[DIR_MAX_LEVELS] = {0};    // force brick depth per level, 0 = heuristic
+    int tune_zchunk[DIR_MAX_LEVELS] = {0};   // smoothing z chunk per level, 0 = one wave
     char* final_field = nullptr;
     bool have_field = false;
     bool pending = false;
@@ -178,20 +189,27 @@ static int ensure(dir_ctx* c, void** p, size_t bytes) {
     return DIR_OK;
 }
 
-// dense float volume(s) (host or device) -> pitched volume(s) of the context type
-static int import_dense(dir_ctx* c, const float* src, int on_device, char* dst, const Grid3& g,
-                        int ncomp, cudaStream_t s) {
+// Dense volume(s) (host or device) of element size src_esz (4 = float,
+// 2 = int16) -> pitched volume(s) of storage type dst_type.  Same element type:
+// a 2-D copy (exact); float -> bf16 / double: through the import kernel.
+static int import_dense(dir_ctx* c, const void* src, int on_device, int src_esz, char* dst,
+                        int dst_type, const Grid3& g, int ncomp, cudaStream_t s) {
     const size_t n = (size_t)g.nx * g.ny * g.nz;
-    if (!c->fp64) {
-        const size_t w = (size_t)g.nx * sizeof(float);
+    const size_t dst_esz = dst_type == dirk::kStoreF64 ? 8 : (dst_type == dirk::kStoreF32 ? 4 : 2);
+    const bool same = (src_esz == 4 && dst_type == dirk::kStoreF32) ||
+                      (src_esz == 2 && dst_type == dirk::kStoreI16);
+    if (same) {
+        const size_t w = (size_t)g.nx * src_esz;
         for (int comp = 0; comp < ncomp; ++comp)
-            CK(c, cudaMemcpy2DAsync(dst + comp * g.cs * c->esz, (size_t)g.px * sizeof(float),
-                                    src + comp * n, w, w, (size_t)g.ny * g.nz,
+            CK(c, cudaMemcpy2DAsync(dst + comp * g.cs * dst_esz, (size_t)g.px * dst_esz,
+                                    static_cast<const char*>(src) + comp * n * src_esz, w, w,
+                                    (size_t)g.ny * g.nz,
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                     s));
         return DIR_OK;
     }
-    const float* dsrc = src;
+    if (src_esz != 4) return DIR_EUNSUPPORTED;
+    const float* dsrc = static_cast<const float*>(src);
     if (!on_device) {
         const int rc = ensure(c, (void**)&c->stage_f32, 3 * n * sizeof(float));
         if (rc != DIR_OK) return rc;
@@ -199,13 +217,15 @@ static int import_dense(dir_ctx* c, const float* src, int on_device, char* dst, 
                               s));
         dsrc = c->stage_f32;
     }
-    CK(c, dirk::launch_import(true, dsrc, dst, g, ncomp, s));
+    CK(c, dirk::launch_import(dst_type == dirk::kStoreF64, dst_type, dsrc, dst, g, ncomp, s));
     return DIR_OK;
 }
 
 static int upload_pair(dir_ctx* c, const void* S, const void* M, int on_device, cudaStream_t s) {
-    int rc = import_dense(c, (const float*)S, on_device, c->lv[0].S, c->lv[0].g, 1, s);
-    if (rc == DIR_OK) rc = import_dense(c, (const float*)M, on_device, c->lv[0].M, c->lv[0].g, 1, s);
+    const int se = c->input_dtype == DIR_I16 ? 2 : 4;
+    int rc = import_dense(c, S, on_device, se, c->lv[0].S, c->img0_type, c->lv[0].g, 1, s);
+    if (rc == DIR_OK)
+        rc = import_dense(c, M, on_device, se, c->lv[0].M, c->img0_type, c->lv[0].g, 1, s);
     return rc;
 }
 
@@ -238,6 +258,9 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.stop_iter = nullptr;
             sa.iter = 0;
             sa.err = c->derr;
+            sa.in_type = c->img_type(l - 1);
+            sa.out_type = c->real_type;
+            sa.zchunk = 0;
             CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
             CK(c, dirk::launch_decimate(f64, c->B, gf, img ? c->lv[l].M : c->lv[l].S, gc, s));
             c->launches += 2;
@@ -253,14 +276,14 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         const Grid3& g = c->lv[l].g;
         if (lc == 0) {
             if (c->p.init_field) {
-                const int rc = import_dense(c, c->p.init_field, 1, cur, g, 3, s);
+                const int rc = import_dense(c, c->p.init_field, 1, 4, cur, c->field_type, g, 3, s);
                 if (rc != DIR_OK) return rc;
-                if (f64) c->launches += 1;
+                if (c->field_type != dirk::kStoreF32) c->launches += 1;
             } else {
-                CK(c, cudaMemsetAsync(cur, 0, c->esz * 3 * (size_t)g.cs, s));
+                CK(c, cudaMemsetAsync(cur, 0, c->fesz * 3 * (size_t)g.cs, s));
             }
         } else {
-            CK(c, dirk::launch_upsample(f64, cur, c->lv[l + 1].g, oth, g, s));
+            CK(c, dirk::launch_upsample(f64, c->field_type, cur, c->lv[l + 1].g, oth, g, s));
             c->launches += 1;
             char* t = cur;
             cur = oth;
@@ -273,16 +296,22 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.g = g;
         fa.alpha2 = c->p.alpha * c->p.alpha;
         fa.stop_iter = c->ctl + lc;
-        fa.depth = dirk::force_brick_depth(g, c->num_sms, 4);
+        fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms, 4);
+        fa.img_type = c->img_type(l);
+        fa.field_type = c->field_type;
         dirk::SmoothArgs sa;
         sa.g = g;
         sa.ncomp = 3;
         sa.taps = c->taps;
         sa.stop_iter = c->ctl + lc;
         sa.err = c->derr;
+        sa.in_type = c->field_type;
+        sa.out_type = c->field_type;
+        sa.zchunk = c->tune_zchunk[l];
         const bool timed = c->p.timing && l == 0;
         const int n = c->p.iters[lc];
-        const bool fused = c->p.fuse && c->p.stop_mode == 0 && dirk::fused_supported(c->variant);
+        const bool fused = c->p.fuse && c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
+                           c->field_type == c->real_type && c->img_type(l) == c->real_type;
         if (fused && n > 0) {
             // iteration 0 from u, iterations 1..n-1 from the previous v with the
             // smoothing folded in, then one smoothing of the last v
@@ -362,7 +391,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         }
     }
     if (c->variant == DIR_INVERSE_CONSISTENT) {
-        CK(c, dirk::launch_ic_invert(f64, cur, oth, c->lv[0].g, kIcInvertSteps, s));
+        CK(c, dirk::launch_ic_invert(f64, c->field_type, cur, oth, c->lv[0].g, kIcInvertSteps, s));
         c->launches += 1;
         c->final_field = oth;
     } else {
@@ -419,12 +448,28 @@ static int validate_params(const dir_params* p) {
     if (!isfinite(p->alpha)) return DIR_EINVAL;
     if (p->stop_mode != 0 && p->stop_mode != 1) return DIR_EINVAL;
     if (p->stop_mode == 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
-    if (p->field_dtype != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->precision != DIR_F32 && p->precision != DIR_F64) return DIR_EUNSUPPORTED;
+    if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
+    if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
     if (p->fuse != 0 && p->fuse != 1) return DIR_EINVAL;
     return DIR_OK;
 }
+
+// Storage of images and fields from the requested dtypes (validated already).
+static void setup_storage(dir_ctx* c, dir_dtype image_dtype) {
+    c->fp64 = (c->p.precision == DIR_F64);
+    c->esz = c->fp64 ? sizeof(double) : sizeof(float);
+    c->real_type = c->fp64 ? dirk::kStoreF64 : dirk::kStoreF32;
+    c->input_dtype = image_dtype;
+    c->img0_type = image_dtype == DIR_I16 ? dirk::kStoreI16 : c->real_type;
+    c->iesz0 = image_dtype == DIR_I16 ? 2 : c->esz;
+    c->field_type = c->fp64 ? dirk::kStoreF64
+                            : (c->p.field_dtype == DIR_BF16 ? dirk::kStoreBF16 : dirk::kStoreF32);
+    c->fesz = c->field_type == dirk::kStoreF64 ? 8 : (c->field_type == dirk::kStoreF32 ? 4 : 2);
+}
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 extern "C" {
 
@@ -476,7 +521,7 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         g_create_error = "bad variant";
         return DIR_EINVAL;
     }
-    if (image_dtype != DIR_F32) {
+    if (image_dtype != DIR_F32 && image_dtype != DIR_I16) {
         g_create_error = "image dtype not supported by this build";
         return DIR_EUNSUPPORTED;
     }
@@ -490,6 +535,10 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         g_create_error = "bad params";
         return prc;
     }
+    if (image_dtype == DIR_I16 && p.precision != DIR_F32) {
+        g_create_error = "int16 images need single-precision arithmetic";
+        return DIR_EUNSUPPORTED;
+    }
 
     dir_ctx* c = new (std::nothrow) dir_ctx();
     if (!c) return DIR_ENOMEM;
@@ -499,8 +548,7 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
     }
     c->variant = (int)variant;
     c->p = p;
-    c->fp64 = (p.precision == DIR_F64);
-    c->esz = c->fp64 ? sizeof(double) : sizeof(float);
+    setup_storage(c, image_dtype);
     c->stream = (cudaStream_t)cuda_stream;
     c->levels = p.levels;
     make_taps(p.sigma, &c->taps);
@@ -520,10 +568,14 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
 
     // level grids and one pool for all pyramid images
     int nx = dims[0], ny = dims[1], nz = dims[2];
-    size_t pool = 0;
+    size_t pool = 0;  // bytes
+    size_t img_off[DIR_MAX_LEVELS][2];
     for (int l = 0; l < c->levels; ++l) {
         c->lv[l].g = make_grid(nx, ny, nz);
-        pool += 2 * (size_t)c->lv[l].g.cs;
+        for (int k = 0; k < 2; ++k) {
+            img_off[l][k] = pool;
+            pool = align256(pool + (size_t)c->lv[l].g.cs * c->img_esz(l));
+        }
         nx = (nx + 1) / 2;
         ny = (ny + 1) / 2;
         nz = (nz + 1) / 2;
@@ -537,9 +589,9 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
     for (int l = 0; l < c->levels; ++l) c->total_iters += p.iters[l];
     const size_t nred = (size_t)(c->total_iters > 0 ? c->total_iters : 1);
     cudaStream_t st = c->stream;
-    if (cudaMallocAsync(&c->img_pool, pool * c->esz, st) != cudaSuccess ||
-        cudaMallocAsync(&c->A, field * c->esz, st) != cudaSuccess ||
-        cudaMallocAsync(&c->B, field * c->esz, st) != cudaSuccess ||
+    if (cudaMallocAsync(&c->img_pool, pool, st) != cudaSuccess ||
+        cudaMallocAsync(&c->A, field * c->fesz, st) != cudaSuccess ||
+        cudaMallocAsync(&c->B, field * c->fesz, st) != cudaSuccess ||
         cudaMallocAsync(&c->red, 3 * nred * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync(&c->lhist, nred * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync(&c->ctl, DIR_MAX_LEVELS * sizeof(int), st) != cudaSuccess ||
@@ -548,12 +600,9 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         g_create_error = "device allocation failed";
         return fail(DIR_ENOMEM);
     }
-    size_t at = 0;
     for (int l = 0; l < c->levels; ++l) {
-        c->lv[l].S = c->img_pool + at * c->esz;
-        at += c->lv[l].g.cs;
-        c->lv[l].M = c->img_pool + at * c->esz;
-        at += c->lv[l].g.cs;
+        c->lv[l].S = c->img_pool + img_off[l][0];
+        c->lv[l].M = c->img_pool + img_off[l][1];
     }
     e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -573,7 +622,7 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
             }
         }
     }
-    e = cudaMemsetAsync(c->img_pool, 0, pool * c->esz, c->stream);
+    e = cudaMemsetAsync(c->img_pool, 0, pool, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
     if (e != cudaSuccess) {
         set_err(c, "cudaMemsetAsync", e);
@@ -592,7 +641,7 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
 
 int dir_load(dir_ctx* c, const void* S, const void* M, dir_dtype dt, int on_device) {
     if (!c || !S || !M) return DIR_EINVAL;
-    if (dt != DIR_F32) return DIR_EUNSUPPORTED;
+    if (dt != c->input_dtype) return DIR_EUNSUPPORTED;
     if (c->pending) return DIR_ESTATE;
     const int rc = upload_pair(c, S, M, on_device, c->stream);
     if (rc != DIR_OK) return rc;
@@ -732,7 +781,8 @@ static int get_field(dir_ctx* c, void* out, int in_mm, int out_on_device, bool o
     const double sx = in_mm ? c->spacing[0] : 1.0;
     const double sy = in_mm ? c->spacing[1] : 1.0;
     const double sz = in_mm ? c->spacing[2] : 1.0;
-    CK(c, dirk::launch_export_field(c->fp64, c->final_field, g, sx, sy, sz, dst, out_fp64,
+    CK(c, dirk::launch_export_field(c->fp64, c->field_type, c->final_field, g, sx, sy, sz, dst,
+                                    out_fp64,
                                     c->stream));
     if (!out_on_device)
         CK(c, cudaMemcpyAsync(out, dst, 3 * n * osz, cudaMemcpyDeviceToHost, c->stream));
@@ -756,7 +806,7 @@ int dir_warp(dir_ctx* c, const void* img_in, void* img_out, dir_dtype dt, int on
     const size_t n = c->nvox();
     int rc = ensure(c, (void**)&c->stage_img, (size_t)g.cs * c->esz);
     if (rc != DIR_OK) return rc;
-    rc = import_dense(c, (const float*)img_in, on_device, c->stage_img, g, 1, c->stream);
+    rc = import_dense(c, img_in, on_device, 4, c->stage_img, c->real_type, g, 1, c->stream);
     if (rc != DIR_OK) return rc;
     float* dst = (float*)img_out;
     if (!on_device) {
@@ -764,7 +814,8 @@ int dir_warp(dir_ctx* c, const void* img_in, void* img_out, dir_dtype dt, int on
         if (rc != DIR_OK) return rc;
         dst = c->stage_f32;
     }
-    CK(c, dirk::launch_warp(c->fp64, c->stage_img, c->final_field, g, dst, c->stream));
+    CK(c, dirk::launch_warp(c->fp64, c->field_type, c->stage_img, c->final_field, g, dst,
+                            c->stream));
     if (!on_device)
         CK(c, cudaMemcpyAsync(img_out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -793,6 +844,272 @@ const char* dir_version(void) { return "gb300-demons 0.2 (sm_103a)"; }
 }  // extern "C"
 
 // ------------------------------------------------------------------------
+// Batched registrations and launch-shape autotuning.
+//
+// dir_batch_create captures the registrations of many contexts into one CUDA
+// graph: the contexts are spread over K branches (longest job first onto the
+// least loaded branch), the branches run concurrently on the GPU, and one
+// graph launch replays the whole batch.  Small volumes and coarse pyramid
+// levels, each of which leaves most SMs idle, then fill the GPU together.
+//
+// dir_autotune times, per pyramid level of a context, the force kernel's brick
+// depth (1, 2, 4, 8 voxels per thread along z) and the smoothing kernel's z
+// chunk (planes per block), keeps the fastest of each and drops the context's
+// captured graph so that the next registration uses them.
+// ------------------------------------------------------------------------
+struct dir_batch {
+    std::vector<dir_ctx*> ctxs;
+    cudaStream_t stream = nullptr;       // the caller's stream: where the graph runs
+    cudaStream_t origin = nullptr;       // capture helpers
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int branches = 1;
+};
+
+static double ctx_work(const dir_ctx* c) {
+    double w = 0.0;
+    for (int lc = 0; lc < c->levels; ++lc) {
+        const Grid3& g = c->lv[c->levels - 1 - lc].g;
+        w += (double)g.nx * g.ny * g.nz * c->p.iters[lc];
+    }
+    return c->variant == DIR_INVERSE_CONSISTENT ? 1.4 * w : w;
+}
+
+static void batch_release(dir_batch* b) {
+    if (!b) return;
+    if (b->stream || b->origin) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t s : b->br) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
+}
+
+#define BK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            set_err(nullptr, #call, e_);              \
+            batch_release(b);                         \
+            return DIR_ECUDA;                         \
+        }                                             \
+    } while (0)
+
+extern "C" int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, int branches,
+                                void* cuda_stream) {
+    g_create_error.clear();
+    if (!out) return DIR_EINVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1 || branches < 1) return DIR_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || ctxs[i]->pending || ctxs[i]->p.timing) {
+            g_create_error = "dir_batch_create: NULL, busy or timed context";
+            return DIR_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) {
+                g_create_error = "dir_batch_create: a context appears twice";
+                return DIR_EINVAL;
+            }
+    }
+    dir_batch* b = new (std::nothrow) dir_batch();
+    if (!b) return DIR_ENOMEM;
+    b->ctxs.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->branches = branches < n ? branches : n;
+    BK(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BK(cudaEventCreate(&b->t0));
+    BK(cudaEventCreate(&b->t1));
+    b->br.resize(b->branches, nullptr);
+    b->join.resize(b->branches, nullptr);
+    for (int k = 0; k < b->branches; ++k) {
+        BK(cudaStreamCreateWithFlags(&b->br[k], cudaStreamNonBlocking));
+        BK(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming));
+    }
+    // longest job first onto the least loaded branch
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && ctx_work(ctxs[order[j]]) > ctx_work(ctxs[order[j - 1]]); --j) {
+            const int t = order[j];
+            order[j] = order[j - 1];
+            order[j - 1] = t;
+        }
+    std::vector<double> load(b->branches, 0.0);
+    std::vector<int> branch_of(n, 0);
+    for (int i : order) {
+        int best = 0;
+        for (int k = 1; k < b->branches; ++k)
+            if (load[k] < load[best]) best = k;
+        branch_of[i] = best;
+        load[best] += ctx_work(ctxs[i]);
+    }
+    BK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    int rc = DIR_OK;
+    cudaError_t ce = cudaEventRecord(b->fork, b->origin);
+    for (int k = 0; k < b->branches && ce == cudaSuccess; ++k)
+        ce = cudaStreamWaitEvent(b->br[k], b->fork, 0);
+    for (int i : order) {
+        if (ce != cudaSuccess || rc != DIR_OK) break;
+        rc = enqueue_registration(ctxs[i], b->br[branch_of[i]], true);
+        if (rc != DIR_OK) g_create_error = ctxs[i]->err;
+    }
+    for (int k = 0; k < b->branches && ce == cudaSuccess; ++k) {
+        ce = cudaEventRecord(b->join[k], b->br[k]);
+        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+    if (rc != DIR_OK || ce != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc == DIR_OK) set_err(nullptr, "batch capture", ce != cudaSuccess ? ce : ee);
+        batch_release(b);
+        return rc != DIR_OK ? rc : DIR_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        b->exec = nullptr;
+        set_err(nullptr, "cudaGraphInstantiate", ei);
+        batch_release(b);
+        return DIR_ECUDA;
+    }
+    *out = b;
+    return DIR_OK;
+}
+
+extern "C" int dir_batch_run(dir_batch* b, float* ms_out) {
+    if (!b) return DIR_EINVAL;
+    for (dir_ctx* c : b->ctxs)
+        if (c->pending) return DIR_ESTATE;
+    cudaError_t e = cudaEventRecord(b->t0, b->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->t1, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "dir_batch_run", e);
+        return DIR_ECUDA;
+    }
+    // per-context results: iterations run, reductions, field ready
+    for (dir_ctx* c : b->ctxs) {
+        c->pending = true;
+        const int rc = dir_sync(c, nullptr);
+        if (rc != DIR_OK) return rc;
+    }
+    if (ms_out) {
+        e = cudaEventElapsedTime(ms_out, b->t0, b->t1);
+        if (e != cudaSuccess) return DIR_ECUDA;
+    }
+    return DIR_OK;
+}
+
+extern "C" void dir_batch_destroy(dir_batch* b) { batch_release(b); }
+
+extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
+    if (!c || reps < 1) return DIR_EINVAL;
+    if (c->pending) return DIR_ESTATE;
+    if (!c->have_field) return DIR_ESTATE;  // needs the pyramid of a finished registration
+    const Grid3& g0 = c->lv[0].g;
+    const size_t fbytes = align256(3 * (size_t)g0.cs * c->fesz);
+    char* scratch = nullptr;  // u, v and the reduction sums of the trial launches
+    if (cudaMallocAsync((void**)&scratch, 2 * fbytes + 256, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "autotune: allocation failed";
+        return DIR_ENOMEM;
+    }
+    void* u = scratch;
+    void* v = scratch + fbytes;
+    double* red = reinterpret_cast<double*>(scratch + 2 * fbytes);
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    int rc = DIR_OK;
+    auto timed = [&](auto&& launch, float* ms) -> int {
+        CK(c, launch());  // warm up (also sets kernel attributes)
+        CK(c, cudaEventRecord(ea, c->stream));
+        for (int r = 0; r < reps; ++r) CK(c, launch());
+        CK(c, cudaEventRecord(eb, c->stream));
+        CK(c, cudaEventSynchronize(eb));
+        CK(c, cudaEventElapsedTime(ms, ea, eb));
+        return DIR_OK;
+    };
+    if (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess) rc = DIR_ECUDA;
+    if (rc == DIR_OK && cudaMemsetAsync(scratch, 0, 2 * fbytes + 256, c->stream) != cudaSuccess)
+        rc = DIR_ECUDA;
+    for (int l = 0; l < c->levels && rc == DIR_OK; ++l) {
+        const Grid3& g = c->lv[l].g;
+        dirk::ForceArgs fa;
+        fa.S = c->lv[l].S;
+        fa.M = c->lv[l].M;
+        fa.u = u;
+        fa.v = v;
+        fa.g = g;
+        fa.alpha2 = c->p.alpha * c->p.alpha;
+        fa.red = red;
+        fa.stop_iter = nullptr;
+        fa.iter = 0;
+        fa.img_type = c->img_type(l);
+        fa.field_type = c->field_type;
+        float best = 1e30f;
+        int best_d = 0;
+        for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {
+            fa.depth = d;
+            float ms = 0.0f;
+            rc = timed([&]() { return dirk::launch_force(c->variant, c->fp64, fa, c->stream); }, &ms);
+            if (rc == DIR_OK && ms < best) {
+                best = ms;
+                best_d = d;
+            }
+        }
+        dirk::SmoothArgs sa;
+        sa.in = v;
+        sa.out = u;
+        sa.g = g;
+        sa.ncomp = 3;
+        sa.taps = c->taps;
+        sa.stop_iter = nullptr;
+        sa.iter = 0;
+        sa.err = c->derr;
+        sa.in_type = c->field_type;
+        sa.out_type = c->field_type;
+        best = 1e30f;
+        int best_z = 0;
+        int cand[16], nc = 0;
+        cand[nc++] = 0;  // one wave (the default)
+        for (int z = 1; z < g.nz && nc < 15; z *= 2) cand[nc++] = z;
+        cand[nc++] = g.nz;
+        for (int k = 0; k < nc && rc == DIR_OK; ++k) {
+            sa.zchunk = cand[k];
+            float ms = 0.0f;
+            rc = timed([&]() { return dirk::launch_smooth(c->fp64, sa, c->num_sms, c->stream); }, &ms);
+            if (rc == DIR_OK && ms < best) {
+                best = ms;
+                best_z = cand[k];
+            }
+        }
+        c->tune_depth[l] = best_d;
+        c->tune_zchunk[l] = best_z;
+        if (shapes_out) {
+            shapes_out[2 * l] = best_d;
+            shapes_out[2 * l + 1] = best_z;
+        }
+    }
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+    cudaFreeAsync(scratch, c->stream);
+    cudaStreamSynchronize(c->stream);
+    if (c->exec) {  // recapture with the new shapes at the next registration
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    return rc;
+}
+
+// ------------------------------------------------------------------------
 // Registration without device allocation (see dir_register_noalloc in dir.h).
 //
 // All scratch -- pyramid images, the two field buffers, reduction rows, stop
@@ -813,8 +1130,6 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
-
-size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 }  // namespace
 
@@ -848,8 +1163,7 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
     c.variant = (int)variant;
     c.p = p;
     c.p.use_graph = 0;
-    c.fp64 = (p.precision == DIR_F64);
-    c.esz = c.fp64 ? sizeof(double) : sizeof(float);
+    setup_storage(&c, DIR_F32);
     c.stream = (cudaStream_t)cuda_stream;
     c.levels = p.levels;
     make_taps(p.sigma, &c.taps);
@@ -862,9 +1176,9 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
     for (int l = 0; l < c.levels; ++l) {
         c.lv[l].g = make_grid(nx, ny, nz);
         lvl_off[l][0] = at;
-        at = align256(at + (size_t)c.lv[l].g.cs * c.esz);
+        at = align256(at + (size_t)c.lv[l].g.cs * c.img_esz(l));
         lvl_off[l][1] = at;
-        at = align256(at + (size_t)c.lv[l].g.cs * c.esz);
+        at = align256(at + (size_t)c.lv[l].g.cs * c.img_esz(l));
         nx = (nx + 1) / 2;
         ny = (ny + 1) / 2;
         nz = (nz + 1) / 2;
@@ -875,9 +1189,9 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
     for (int l = 0; l < c.levels; ++l) c.total_iters += p.iters[l];
     const size_t nred = (size_t)(c.total_iters > 0 ? c.total_iters : 1);
     const size_t offA = at;
-    at = align256(at + field * c.esz);
+    at = align256(at + field * c.fesz);
     const size_t offB = at;
-    at = align256(at + field * c.esz);
+    at = align256(at + field * c.fesz);
     const size_t offRed = at;
     at = align256(at + 3 * nred * sizeof(double));
     const size_t offL = at;
@@ -936,8 +1250,9 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
 
     int rc = upload_pair(&c, static_img, moving_img, 1, c.stream);
     if (rc == DIR_OK) rc = enqueue_registration(&c, c.stream, false);
-    if (rc == DIR_OK && dirk::launch_export_field(c.fp64, c.final_field, c.lv[0].g, 1.0, 1.0, 1.0,
-                                                  field_out, false, c.stream) != cudaSuccess)
+    if (rc == DIR_OK && dirk::launch_export_field(c.fp64, c.field_type, c.final_field, c.lv[0].g,
+                                                  1.0, 1.0, 1.0, field_out, false,
+                                                  c.stream) != cudaSuccess)
         rc = DIR_ECUDA;
     int ctl[DIR_MAX_LEVELS + 1] = {0};
     if (rc == DIR_OK &&

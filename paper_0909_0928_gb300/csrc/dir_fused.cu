@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
                 const Real ux = utile[(0 * STY + fy) * STX + fx];
                 const Real uy = utile[(1 * STY + fy) * STX + fx];
                 const Real uz = utile[(2 * STY + fy) * STX + fx];
-                const Real wv = trilinear(M, g, x, ux, y, uy, zo, uz);
+                const Real d = trilinear(M, g, x, ux, y, uy, zo, uz, s_0);  // W - S
                 const int ro = offs(g, 0, y, zo);
                 const Real gsx = Real(0.5) * (__ldg(S + ro + xp) - __ldg(S + ro + xm));
                 const Real gsy =
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
                     const Real mz = Real(0.5) * (m_p1 - m_m1);
                     bm = r_sqrt(mx * mx + my * my + mz * mz);
                 }
-                const Real d = wv - s_0;
                 Real dx, dy, dz;
                 demons_force<Real, V>(d, gsx, gsy, gsz, Real(0), Real(0), Real(0), bm, Real(0), dx,
                                       dy, dz);

@@ -9,6 +9,9 @@
 
 namespace dirk {
 
+// storage types of images and fields on the device
+constexpr int kStoreF32 = 0, kStoreI16 = 1, kStoreBF16 = 3, kStoreF64 = 4;
+
 // Force + update + reductions of one demons iteration at one level
 // (Sec. 2.5 interpolation, gradient and displacement kernels fused):
 //   v = u - dr(u),  red[0..2] += {sum d^2, sum |du|, sum |u|}.
@@ -24,6 +27,8 @@ struct ForceArgs {
     const int* stop_iter;
     int iter;
     int depth;           // voxels per thread along z: 1, 2, 4 or 8
+    int img_type;        // storage of S and M at this level (kStore*)
+    int field_type;      // storage of u and v (kStore*)
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
 int force_brick_depth(const Grid3& g, int num_sms, int waves);
@@ -39,6 +44,9 @@ struct SmoothArgs {
     const int* stop_iter;
     int iter;
     int* err;            // device error word (kErr* bits)
+    int in_type;         // storage of in (kStore*)
+    int out_type;        // storage of out
+    int zchunk;          // planes per block; 0 = one wave of resident blocks
 };
 cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s);
 
@@ -59,25 +67,27 @@ struct FusedArgs {
 bool fused_supported(int variant);
 cudaError_t launch_fused(int variant, bool fp64, const FusedArgs& a, int num_sms, cudaStream_t s);
 
-// out(i, j, k) = in(2i, 2j, 2k)   (pyramid decimation, Sec. 2.3)
+// out(i, j, k) = in(2i, 2j, 2k)   (pyramid decimation, Sec. 2.3; float or double)
 cudaError_t launch_decimate(bool fp64, const void* in, const Grid3& gin, void* out,
                             const Grid3& gout, cudaStream_t s);
+// The field kernels below take the field storage type ftype (kStoreF32,
+// kStoreBF16 with float arithmetic; kStoreF64 with double).
 // fine(x) = 2 * trilinear(coarse, x / 2), per component (Sec. 2.3)
-cudaError_t launch_upsample(bool fp64, const void* coarse, const Grid3& gc, void* fine,
+cudaError_t launch_upsample(bool fp64, int ftype, const void* coarse, const Grid3& gc, void* fine,
                             const Grid3& gf, cudaStream_t s);
-// out(x) = img(x + u(x)); out written dense float (x-contiguous, no pitch)
-cudaError_t launch_warp(bool fp64, const void* img, const void* u, const Grid3& g,
+// out(x) = img(x + u(x)); img in the arithmetic type, out written dense float
+cudaError_t launch_warp(bool fp64, int ftype, const void* img, const void* u, const Grid3& g,
                         float* out_dense, cudaStream_t s);
 // u(y) = 2 h(x*), x* = y + h(x*) by `steps` fixed-point steps (Eq. 6 output)
-cudaError_t launch_ic_invert(bool fp64, const void* h, void* u, const Grid3& g, int steps,
-                             cudaStream_t s);
+cudaError_t launch_ic_invert(bool fp64, int ftype, const void* h, void* u, const Grid3& g,
+                             int steps, cudaStream_t s);
 // dense[c*N + i + nx*(j + ny*k)] = scale[c] * field[c*cs + pitched(i,j,k)],
 // written as float (out_fp64 = false) or double
-cudaError_t launch_export_field(bool fp64, const void* field, const Grid3& g, double sx,
+cudaError_t launch_export_field(bool fp64, int ftype, const void* field, const Grid3& g, double sx,
                                 double sy, double sz, void* dense, bool out_fp64, cudaStream_t s);
-// pitched[c] = dense float input, for ncomp components (c*N apart in dense)
-cudaError_t launch_import(bool fp64, const float* dense, void* pitched, const Grid3& g, int ncomp,
-                          cudaStream_t s);
+// pitched[c] = dense float input converted to out_type, for ncomp components
+cudaError_t launch_import(bool fp64, int out_type, const float* dense, void* pitched,
+                          const Grid3& g, int ncomp, cudaStream_t s);
 // relative-norm stop test of Sec. 2.4 for iteration t of a level
 cudaError_t launch_stop_test(const double* red, double* lhist, int t, int level_first, int window,
                              double eps, int* stop_iter, int iter_in_level, cudaStream_t s);

@@ -25,8 +25,8 @@ __global__ void decimate_kernel(const Real* __restrict__ in, Grid3 gi, Real* __r
     out[offs(go, x, y, z)] = __ldg(in + offs(gi, 2 * x, 2 * y, 2 * z));
 }
 
-template <typename Real>
-__global__ void upsample_kernel(const Real* __restrict__ coarse, Grid3 gc, Real* __restrict__ fine,
+template <typename Real, typename TF>
+__global__ void upsample_kernel(const TF* __restrict__ coarse, Grid3 gc, TF* __restrict__ fine,
                                 Grid3 gf) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
@@ -36,49 +36,49 @@ __global__ void upsample_kernel(const Real* __restrict__ coarse, Grid3 gc, Real*
     const long long o = (long long)offs(gf, x, y, z);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        fine[o + c * gf.cs] =
-            Real(2) * trilinear(coarse + c * gc.cs, gc, x >> 1, hx, y >> 1, hy, z >> 1, hz);
+        fine[o + c * gf.cs] = st_as<TF>(
+            Real(2) * trilinear<Real>(coarse + c * gc.cs, gc, x >> 1, hx, y >> 1, hy, z >> 1, hz));
 }
 
-template <typename Real>
-__global__ void warp_kernel(const Real* __restrict__ img, const Real* __restrict__ u, Grid3 g,
+template <typename Real, typename TF>
+__global__ void warp_kernel(const Real* __restrict__ img, const TF* __restrict__ u, Grid3 g,
                             float* __restrict__ out) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const long long o = (long long)offs(g, x, y, z);
-    const Real w = trilinear(img, g, x, __ldg(u + o), y, __ldg(u + o + g.cs), z,
-                             __ldg(u + o + 2 * g.cs));
+    const Real w = trilinear<Real>(img, g, x, ldg_as<Real>(u + o), y, ldg_as<Real>(u + o + g.cs),
+                                   z, ldg_as<Real>(u + o + 2 * g.cs));
     out[(long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z)] = (float)w;
 }
 
-template <typename Real>
-__global__ void ic_invert_kernel(const Real* __restrict__ h, Real* __restrict__ u, Grid3 g,
+template <typename Real, typename TF>
+__global__ void ic_invert_kernel(const TF* __restrict__ h, TF* __restrict__ u, Grid3 g,
                                  int steps) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
-    const Real* hx = h;
-    const Real* hy = h + g.cs;
-    const Real* hz = h + 2 * g.cs;
+    const TF* hx = h;
+    const TF* hy = h + g.cs;
+    const TF* hz = h + 2 * g.cs;
     // x* = y + a with a = h(x*), iterated from a = 0
     Real ax = 0, ay = 0, az = 0;
     for (int s = 0; s < steps; ++s) {
-        const Real nx_ = trilinear(hx, g, x, ax, y, ay, z, az);
-        const Real ny_ = trilinear(hy, g, x, ax, y, ay, z, az);
-        const Real nz_ = trilinear(hz, g, x, ax, y, ay, z, az);
+        const Real nx_ = trilinear<Real>(hx, g, x, ax, y, ay, z, az);
+        const Real ny_ = trilinear<Real>(hy, g, x, ax, y, ay, z, az);
+        const Real nz_ = trilinear<Real>(hz, g, x, ax, y, ay, z, az);
         ax = nx_;
         ay = ny_;
         az = nz_;
     }
     const long long o = (long long)offs(g, x, y, z);
-    u[o] = Real(2) * trilinear(hx, g, x, ax, y, ay, z, az);
-    u[o + g.cs] = Real(2) * trilinear(hy, g, x, ax, y, ay, z, az);
-    u[o + 2 * g.cs] = Real(2) * trilinear(hz, g, x, ax, y, ay, z, az);
+    u[o] = st_as<TF>(Real(2) * trilinear<Real>(hx, g, x, ax, y, ay, z, az));
+    u[o + g.cs] = st_as<TF>(Real(2) * trilinear<Real>(hy, g, x, ax, y, ay, z, az));
+    u[o + 2 * g.cs] = st_as<TF>(Real(2) * trilinear<Real>(hz, g, x, ax, y, ay, z, az));
 }
 
-template <typename Real, typename Out>
-__global__ void export_kernel(const Real* __restrict__ f, Grid3 g, double sx, double sy, double sz,
+template <typename Real, typename TF, typename Out>
+__global__ void export_kernel(const TF* __restrict__ f, Grid3 g, double sx, double sy, double sz,
                               Out* __restrict__ dense) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
@@ -86,13 +86,13 @@ __global__ void export_kernel(const Real* __restrict__ f, Grid3 g, double sx, do
     const long long n = (long long)g.nx * g.ny * g.nz;
     const long long o = (long long)offs(g, x, y, z);
     const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-    dense[d] = (Out)((Real)sx * f[o]);
-    dense[d + n] = (Out)((Real)sy * f[o + g.cs]);
-    dense[d + 2 * n] = (Out)((Real)sz * f[o + 2 * g.cs]);
+    dense[d] = (Out)((Real)sx * ld_as<Real>(f + o));
+    dense[d + n] = (Out)((Real)sy * ld_as<Real>(f + o + g.cs));
+    dense[d + 2 * n] = (Out)((Real)sz * ld_as<Real>(f + o + 2 * g.cs));
 }
 
-template <typename Real>
-__global__ void import_kernel(const float* __restrict__ dense, Real* __restrict__ f, Grid3 g,
+template <typename Real, typename TF>
+__global__ void import_kernel(const float* __restrict__ dense, TF* __restrict__ f, Grid3 g,
                               int ncomp) {
     const int x = blockIdx.x * MTX + threadIdx.x, y = blockIdx.y * MTY + threadIdx.y;
     const int z = blockIdx.z;
@@ -100,7 +100,7 @@ __global__ void import_kernel(const float* __restrict__ dense, Real* __restrict_
     const long long n = (long long)g.nx * g.ny * g.nz;
     const long long o = (long long)offs(g, x, y, z);
     const long long d = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-    for (int c = 0; c < ncomp; ++c) f[o + c * g.cs] = (Real)dense[d + c * n];
+    for (int c = 0; c < ncomp; ++c) f[o + c * g.cs] = st_as<TF>((Real)dense[d + c * n]);
 }
 
 // Sec. 2.4: l(t) = sum|du| / sum|u|; stop the level after iteration t when
@@ -118,64 +118,81 @@ __global__ void stop_test_kernel(const double* __restrict__ red, double* lhist, 
     }
 }
 
-#define DIR_DISPATCH(fp64, CALL)          \
-    do {                                  \
-        if (fp64) {                       \
-            using Real = double;          \
-            CALL;                         \
-        } else {                          \
-            using Real = float;           \
-            CALL;                         \
-        }                                 \
+// Dispatch on (arithmetic, field storage): double/double, float/float,
+// float/bf16.  `CALL` sees the types as Real and TF.
+#define DIR_DISPATCH_F(fp64, ftype, CALL)                      \
+    do {                                                       \
+        if (fp64) {                                            \
+            if (ftype != kStoreF64) return cudaErrorInvalidValue; \
+            using Real = double;                               \
+            using TF = double;                                 \
+            CALL;                                              \
+        } else if (ftype == kStoreBF16) {                      \
+            using Real = float;                                \
+            using TF = bf16;                                   \
+            CALL;                                              \
+        } else if (ftype == kStoreF32) {                       \
+            using Real = float;                                \
+            using TF = float;                                  \
+            CALL;                                              \
+        } else {                                               \
+            return cudaErrorInvalidValue;                      \
+        }                                                      \
     } while (0)
 
 cudaError_t launch_decimate(bool fp64, const void* in, const Grid3& gin, void* out,
                             const Grid3& gout, cudaStream_t s) {
-    DIR_DISPATCH(fp64, (decimate_kernel<Real><<<grid_for(gout), dim3(MTX, MTY), 0, s>>>(
-                           static_cast<const Real*>(in), gin, static_cast<Real*>(out), gout)));
+    if (fp64)
+        decimate_kernel<double><<<grid_for(gout), dim3(MTX, MTY), 0, s>>>(
+            static_cast<const double*>(in), gin, static_cast<double*>(out), gout);
+    else
+        decimate_kernel<float><<<grid_for(gout), dim3(MTX, MTY), 0, s>>>(
+            static_cast<const float*>(in), gin, static_cast<float*>(out), gout);
     return cudaGetLastError();
 }
 
-cudaError_t launch_upsample(bool fp64, const void* coarse, const Grid3& gc, void* fine,
+cudaError_t launch_upsample(bool fp64, int ftype, const void* coarse, const Grid3& gc, void* fine,
                             const Grid3& gf, cudaStream_t s) {
-    DIR_DISPATCH(fp64, (upsample_kernel<Real><<<grid_for(gf), dim3(MTX, MTY), 0, s>>>(
-                           static_cast<const Real*>(coarse), gc, static_cast<Real*>(fine), gf)));
+    DIR_DISPATCH_F(fp64, ftype, (upsample_kernel<Real, TF><<<grid_for(gf), dim3(MTX, MTY), 0, s>>>(
+                                    static_cast<const TF*>(coarse), gc, static_cast<TF*>(fine), gf)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp(bool fp64, const void* img, const void* u, const Grid3& g,
+cudaError_t launch_warp(bool fp64, int ftype, const void* img, const void* u, const Grid3& g,
                         float* out_dense, cudaStream_t s) {
-    DIR_DISPATCH(fp64, (warp_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
-                           static_cast<const Real*>(img), static_cast<const Real*>(u), g,
-                           out_dense)));
+    DIR_DISPATCH_F(fp64, ftype, (warp_kernel<Real, TF><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                                    static_cast<const Real*>(img), static_cast<const TF*>(u), g,
+                                    out_dense)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_ic_invert(bool fp64, const void* h, void* u, const Grid3& g, int steps,
-                             cudaStream_t s) {
-    DIR_DISPATCH(fp64, (ic_invert_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
-                           static_cast<const Real*>(h), static_cast<Real*>(u), g, steps)));
+cudaError_t launch_ic_invert(bool fp64, int ftype, const void* h, void* u, const Grid3& g,
+                             int steps, cudaStream_t s) {
+    DIR_DISPATCH_F(fp64, ftype, (ic_invert_kernel<Real, TF><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                                    static_cast<const TF*>(h), static_cast<TF*>(u), g, steps)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_field(bool fp64, const void* field, const Grid3& g, double sx,
+cudaError_t launch_export_field(bool fp64, int ftype, const void* field, const Grid3& g, double sx,
                                 double sy, double sz, void* dense, bool out_fp64, cudaStream_t s) {
     if (out_fp64) {
-        DIR_DISPATCH(fp64, (export_kernel<Real, double><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
-                               static_cast<const Real*>(field), g, sx, sy, sz,
-                               static_cast<double*>(dense))));
+        DIR_DISPATCH_F(fp64, ftype,
+                       (export_kernel<Real, TF, double><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const TF*>(field), g, sx, sy, sz,
+                           static_cast<double*>(dense))));
     } else {
-        DIR_DISPATCH(fp64, (export_kernel<Real, float><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
-                               static_cast<const Real*>(field), g, sx, sy, sz,
-                               static_cast<float*>(dense))));
+        DIR_DISPATCH_F(fp64, ftype,
+                       (export_kernel<Real, TF, float><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                           static_cast<const TF*>(field), g, sx, sy, sz,
+                           static_cast<float*>(dense))));
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_import(bool fp64, const float* dense, void* pitched, const Grid3& g, int ncomp,
-                          cudaStream_t s) {
-    DIR_DISPATCH(fp64, (import_kernel<Real><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
-                           dense, static_cast<Real*>(pitched), g, ncomp)));
+cudaError_t launch_import(bool fp64, int out_type, const float* dense, void* pitched,
+                          const Grid3& g, int ncomp, cudaStream_t s) {
+    DIR_DISPATCH_F(fp64, out_type, (import_kernel<Real, TF><<<grid_for(g), dim3(MTX, MTY), 0, s>>>(
+                                       dense, static_cast<TF*>(pitched), g, ncomp)));
     return cudaGetLastError();
 }
 

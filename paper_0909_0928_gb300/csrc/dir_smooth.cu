@@ -16,16 +16,16 @@
 
 namespace dirk {
 
-template <typename Real, int R>
-__global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8>::YT)
+template <typename Real, int R, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8, TIN>::YT)
     smooth_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
     constexpr int NC = 1;
-    using G = StencilGeom<Real, R, NC, 8>;
+    using G = StencilGeom<Real, R, NC, 8, TIN>;
     constexpr int K = G::K, NT = G::YT;
     extern __shared__ unsigned char smem_raw[];
     const Grid3 g = a.g;
-    Real* __restrict__ out = static_cast<Real*>(a.out);
+    TOUT* __restrict__ out = static_cast<TOUT*>(a.out);
     Real w[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) w[t] = tap<Real>(a.taps, t);
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8>::YT)
     const int z1 = min(z0 + zchunk, g.nz);
     out += (long long)comp * g.cs;
 
-    PlanePipe<Real, R, NC, 8> pipe;
+    PlanePipe<Real, R, NC, 8, TIN> pipe;
     pipe.setup(smem_raw, g, x0, y0, z0, z1, comp);
     pipe.start(&tmap, g, tid);
 
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8>::YT)
 #pragma unroll
             for (int r = 0; r < YW; ++r) {
                 const int y = y0 + q_own * YW + r;
-                if (y < g.ny) out[offs(g, x, y, zo)] = zpass<Real, R>(w, ring, r);
+                if (y < g.ny) out[offs(g, x, y, zo)] = st_as<TOUT>(zpass<Real, R>(w, ring, r));
             }
         }
         // no barrier here: the next step's __syncthreads_or orders these reads
@@ -66,46 +66,58 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8>::YT)
     }
 }
 
-template <typename Real, int R>
-static cudaError_t launch_r(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    using G = StencilGeom<Real, R, 1, 8>;
+template <typename Real, int R, typename TIN, typename TOUT>
+static cudaError_t launch_rt(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    using G = StencilGeom<Real, R, 1, 8, TIN>;
     CUtensorMap map;
-    if (!make_plane_map<Real, R, 1>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
+    if (!make_plane_map<Real, R, 1, TIN>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            smooth_kernel<Real, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::BASE_SMEM);
+        const cudaError_t e = cudaFuncSetAttribute(smooth_kernel<Real, R, TIN, TOUT>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   G::BASE_SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R>, G::YT,
-                                                  G::BASE_SMEM);
-    const int zc = stencil_zchunk(a.g, per_sm, num_sms, a.ncomp);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R, TIN, TOUT>,
+                                                  G::YT, G::BASE_SMEM);
+    int zc = a.zchunk > 0 ? a.zchunk : stencil_zchunk(a.g, per_sm, num_sms, a.ncomp);
+    if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
     const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY, chunks * a.ncomp);
-    smooth_kernel<Real, R><<<grid, dim3(G::YT, 1, 1), G::BASE_SMEM, s>>>(map, a, zc);
+    smooth_kernel<Real, R, TIN, TOUT><<<grid, dim3(G::YT, 1, 1), G::BASE_SMEM, s>>>(map, a, zc);
     return cudaGetLastError();
 }
 
-template <typename Real>
-static cudaError_t launch_t(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+template <typename Real, typename TIN, typename TOUT>
+static cudaError_t launch_types(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     switch (a.taps.R) {
-        case 1: return launch_r<Real, 1>(a, num_sms, s);
-        case 2: return launch_r<Real, 2>(a, num_sms, s);
-        case 3: return launch_r<Real, 3>(a, num_sms, s);
-        case 4: return launch_r<Real, 4>(a, num_sms, s);
-        case 5: return launch_r<Real, 5>(a, num_sms, s);
-        case 6: return launch_r<Real, 6>(a, num_sms, s);
-        case 7: return launch_r<Real, 7>(a, num_sms, s);
-        case 8: return launch_r<Real, 8>(a, num_sms, s);
+        case 1: return launch_rt<Real, 1, TIN, TOUT>(a, num_sms, s);
+        case 2: return launch_rt<Real, 2, TIN, TOUT>(a, num_sms, s);
+        case 3: return launch_rt<Real, 3, TIN, TOUT>(a, num_sms, s);
+        case 4: return launch_rt<Real, 4, TIN, TOUT>(a, num_sms, s);
+        case 5: return launch_rt<Real, 5, TIN, TOUT>(a, num_sms, s);
+        case 6: return launch_rt<Real, 6, TIN, TOUT>(a, num_sms, s);
+        case 7: return launch_rt<Real, 7, TIN, TOUT>(a, num_sms, s);
+        case 8: return launch_rt<Real, 8, TIN, TOUT>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s) {
     if (a.ncomp != 1 && a.ncomp != 3) return cudaErrorInvalidValue;
-    return fp64 ? launch_t<double>(a, num_sms, s) : launch_t<float>(a, num_sms, s);
+    if (fp64) {
+        if (a.in_type != kStoreF64 || a.out_type != kStoreF64) return cudaErrorInvalidValue;
+        return launch_types<double, double, double>(a, num_sms, s);
+    }
+    if (a.in_type == kStoreF32 && a.out_type == kStoreF32)
+        return launch_types<float, float, float>(a, num_sms, s);
+    if (a.in_type == kStoreI16 && a.out_type == kStoreF32)
+        return launch_types<float, int16_t, float>(a, num_sms, s);
+    if (a.in_type == kStoreBF16 && a.out_type == kStoreBF16)
+        return launch_types<float, bf16, bf16>(a, num_sms, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace dirk

@@ -14,6 +14,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "dir_common.cuh"
 #include "dir_launch.h"
 
@@ -22,28 +24,55 @@ namespace dirk {
 constexpr int STX = 32, STY = 8, YW = 4;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
-template <typename Real>
-struct Vec16;  // 16-byte vector of Real
+// Vector loads of the staged rows: 16 bytes for 4- and 8-byte elements, 8
+// bytes for 2-byte elements (their task offsets are only 8-byte aligned).
+template <typename T>
+struct VecLd;
 template <>
-struct Vec16<float> {
-    using T = float4;
+struct VecLd<float> {
+    using V = float4;
     static constexpr int N = 4;
 };
 template <>
-struct Vec16<double> {
-    using T = double2;
+struct VecLd<double> {
+    using V = double2;
     static constexpr int N = 2;
 };
+template <>
+struct VecLd<int16_t> {
+    using V = uint2;
+    static constexpr int N = 4;
+};
+template <>
+struct VecLd<bf16> {
+    using V = uint2;
+    static constexpr int N = 4;
+};
 
-__device__ __forceinline__ void unpack(const float4& t, float* d) {
+template <typename Real>
+__device__ __forceinline__ void unpack(const float4& t, Real* d) {
     d[0] = t.x;
     d[1] = t.y;
     d[2] = t.z;
     d[3] = t.w;
 }
-__device__ __forceinline__ void unpack(const double2& t, double* d) {
+template <typename Real>
+__device__ __forceinline__ void unpack(const double2& t, Real* d) {
     d[0] = t.x;
     d[1] = t.y;
+}
+template <typename T, typename Real>
+__device__ __forceinline__ void unpack16(const uint2& t, Real* d) {
+    const uint32_t w[2] = {t.x, t.y};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned short h = (unsigned short)(w[k >> 1] >> (16 * (k & 1)));
+        if constexpr (sizeof(T) == 2 && std::is_same<T, int16_t>::value) {
+            d[k] = (Real)(short)h;
+        } else {
+            d[k] = (Real)__bfloat162float(__ushort_as_bfloat16(h));
+        }
+    }
 }
 __device__ __forceinline__ void store4(float* dst, const float* s) {
     *reinterpret_cast<float4*>(dst) = make_float4(s[0], s[1], s[2], s[3]);
@@ -53,18 +82,20 @@ __device__ __forceinline__ void store4(double* dst, const double* s) {
     reinterpret_cast<double2*>(dst)[1] = make_double2(s[2], s[3]);
 }
 
-template <typename Real, int R, int NC, int STAGES_ = 4>
+template <typename Real, int R, int NC, int STAGES_ = 4, typename TIN = Real>
 struct StencilGeom {
     static constexpr int STAGES = STAGES_;
-    static constexpr int HA = (R + 3) / 4 * 4;   // x halo rounded up: TMA x start 16-byte aligned
+    static constexpr int ALIGN = 16 / (int)sizeof(TIN);      // elements per 16 bytes
+    static constexpr int HA = (R + ALIGN - 1) / ALIGN * ALIGN;  // x halo: TMA x start 16-byte aligned
     static constexpr int WB = STX + 2 * HA;      // box width
     static constexpr int H = STY + 2 * R;        // box height
     static constexpr int K = 2 * R + 1;
     static constexpr int YT = STX * NC * (STY / YW);  // y/z tasks: (x, component, row group)
     static constexpr int XL = 4 + 2 * R;              // inputs of one 4-output x task
-    static constexpr int XLV = (HA - R + XL + 3) / 4 * 4;  // loaded span, whole 16-byte vectors
+    static constexpr int VN = VecLd<TIN>::N;
+    static constexpr int XLV = (HA - R + XL + VN - 1) / VN * VN;  // loaded span, whole vectors
     static constexpr int SLOT_ELEMS = NC * H * WB;
-    static constexpr int SLOT_BYTES = SLOT_ELEMS * (int)sizeof(Real);
+    static constexpr int SLOT_BYTES = SLOT_ELEMS * (int)sizeof(TIN);
     static constexpr int SLOT_STRIDE = (SLOT_BYTES + 127) / 128 * 128;
     static constexpr int TXP_BYTES = NC * H * STX * (int)sizeof(Real);
     static constexpr int TXP_STRIDE = (TXP_BYTES + 127) / 128 * 128;
@@ -73,9 +104,9 @@ struct StencilGeom {
 };
 
 // Per-block state of the TMA plane pipeline.
-template <typename Real, int R, int NC, int STAGES_ = 4>
+template <typename Real, int R, int NC, int STAGES_ = 4, typename TIN = Real>
 struct PlanePipe {
-    using G = StencilGeom<Real, R, NC, STAGES_>;
+    using G = StencilGeom<Real, R, NC, STAGES_, TIN>;
     static constexpr int STAGES = STAGES_;
     unsigned char* base;
     Real* txp;
@@ -136,9 +167,9 @@ struct PlanePipe {
         }
         (void)mbar_try_wait(&full[s], parity);
         constexpr int HA = G::HA, WB = G::WB, H = G::H, K = G::K;
-        using V = typename Vec16<Real>::T;
-        constexpr int VN = Vec16<Real>::N;
-        Real* slot = reinterpret_cast<Real*>(base + s * G::SLOT_STRIDE);  // [NC][H][WB]
+        using V = typename VecLd<TIN>::V;
+        constexpr int VN = VecLd<TIN>::N;
+        TIN* slot = reinterpret_cast<TIN*>(base + s * G::SLOT_STRIDE);  // [NC][H][WB]
         if (edge) {
             // replicate boundary: out-of-volume columns first (a thread per
             // row), then out-of-volume rows (a thread per column, rows already
@@ -146,8 +177,8 @@ struct PlanePipe {
             const int lo = max(0, -bx);         // first in-volume column of the box
             const int hi = min(WB, g.nx - bx);  // one past the last
             for (int row = tid; row < NC * H; row += NT) {
-                Real* r = slot + row * WB;
-                const Real left = r[lo], right = r[hi - 1];
+                TIN* r = slot + row * WB;
+                const TIN left = r[lo], right = r[hi - 1];
                 for (int hx = 0; hx < lo; ++hx) r[hx] = left;
                 for (int hx = hi; hx < WB; ++hx) r[hx] = right;
             }
@@ -155,8 +186,8 @@ struct PlanePipe {
             const int rlo = max(0, -by);
             const int rhi = min(H, g.ny - by);
             for (int col = tid; col < NC * WB; col += NT) {
-                Real* cbase = slot + (col / WB) * H * WB + (col % WB);
-                const Real top = cbase[rlo * WB], bot = cbase[(rhi - 1) * WB];
+                TIN* cbase = slot + (col / WB) * H * WB + (col % WB);
+                const TIN top = cbase[rlo * WB], bot = cbase[(rhi - 1) * WB];
                 for (int hy = 0; hy < rlo; ++hy) cbase[hy * WB] = top;
                 for (int hy = rhi; hy < H; ++hy) cbase[hy * WB] = bot;
             }
@@ -165,10 +196,15 @@ struct PlanePipe {
         for (int tk = tid; tk < NC * H * (STX / 4); tk += NT) {
             const int gq = tk % (STX / 4);
             const int row = tk / (STX / 4);  // c * H + r
-            const Real* src = slot + row * WB + 4 * gq;  // 16-byte aligned
+            const TIN* src = slot + row * WB + 4 * gq;  // vector aligned
             Real in[G::XLV];
 #pragma unroll
-            for (int v = 0; v < G::XLV / VN; ++v) unpack(reinterpret_cast<const V*>(src)[v], in + v * VN);
+            for (int v = 0; v < G::XLV / VN; ++v) {
+                if constexpr (sizeof(TIN) == 2)
+                    unpack16<TIN, Real>(reinterpret_cast<const V*>(src)[v], in + v * VN);
+                else
+                    unpack<Real>(reinterpret_cast<const V*>(src)[v], in + v * VN);
+            }
             Real o[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -232,20 +268,31 @@ inline EncodeTiledFn encode_fn() {
 // Tensor map of a pitched (x, y, z, component) array of ncomp components with
 // the plane box of StencilGeom<Real, R, NC> (NC components per copy).
 // Returns false if the driver refuses it.
-template <typename Real, int R, int NC>
+template <typename T>
+inline CUtensorMapDataType tma_type();
+template <>
+inline CUtensorMapDataType tma_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <>
+inline CUtensorMapDataType tma_type<double>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT64; }
+template <>
+inline CUtensorMapDataType tma_type<int16_t>() { return CU_TENSOR_MAP_DATA_TYPE_UINT16; }  // bit copy
+template <>
+inline CUtensorMapDataType tma_type<bf16>() { return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; }
+
+template <typename Real, int R, int NC, typename TIN = Real>
 inline bool make_plane_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
-    using G = StencilGeom<Real, R, NC>;  // the box does not depend on the stage count
+    using G = StencilGeom<Real, R, NC, 4, TIN>;  // the box does not depend on the stage count
+    using Real_ = TIN;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
                                 (cuuint64_t)ncomp};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.px * sizeof(Real),
-                                   (cuuint64_t)g.plane * sizeof(Real),
-                                   (cuuint64_t)g.cs * sizeof(Real)};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * sizeof(Real_),
+                                   (cuuint64_t)g.plane * sizeof(Real_),
+                                   (cuuint64_t)g.cs * sizeof(Real_)};
     const cuuint32_t box[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, 1u, (cuuint32_t)NC};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    return enc(map, sizeof(Real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+    return enc(map, tma_type<TIN>(),
                4, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;

@@ -28,7 +28,7 @@ from dataclasses import field as dc_field
 
 import numpy as np
 
-from . import (DIR_F32, DirParams, dir_create, dir_destroy, dir_get_field, dir_params_default,
+from . import (DIR_F32, DIR_I16, DirParams, dir_create, dir_destroy, dir_get_field, dir_params_default,
                dir_register_async, dir_sync)
 
 
@@ -52,7 +52,7 @@ def footprint_bytes(dims, levels: int, elem: int = 4) -> int:
 @dataclass
 class Request:
     rid: int
-    S: np.ndarray            # (nz, ny, nx) float32, host (pinned or not)
+    S: np.ndarray            # (nz, ny, nx) float32 or int16 HU, host (pinned or not)
     M: np.ndarray
     spacing: tuple
     variant: int
@@ -111,7 +111,8 @@ class Server:
             slot = free_slots[0]
             stream = self.streams[slot]
             req.admitted = self.now()
-            ctx = dir_create(req.S, req.M, req.dims, req.spacing, DIR_F32, False, req.variant,
+            dtype = DIR_I16 if req.S.dtype == np.int16 else DIR_F32
+            ctx = dir_create(req.S, req.M, req.dims, req.spacing, dtype, False, req.variant,
                              req.params, stream)
             dir_register_async(ctx)
             ev = self.torch.cuda.Event()
@@ -176,7 +177,8 @@ _POOL: dict = {}
 
 
 def phantom_pool(sizes, seed: int, a_max_mm: float):
-    """One seeded lung phantom per size (cached): requests reuse them."""
+    """One seeded lung phantom per size (cached), stored as int16 HU: requests
+    reuse them."""
     from phantom import PhantomSpec, make_lung_phantom
     out = []
     for k, dims in enumerate(sizes):
@@ -186,7 +188,8 @@ def phantom_pool(sizes, seed: int, a_max_mm: float):
                                a_max_mm=a_max_mm, compression=0.15, compression_region="lower",
                                n_landmarks=10)
             ph = make_lung_phantom(spec)
-            _POOL[key] = (ph["S"], ph["M"], spec.spacing)
+            _POOL[key] = (np.round(ph["S"]).astype(np.int16), np.round(ph["M"]).astype(np.int16),
+                          spec.spacing)
         out.append(_POOL[key])
     return out
 

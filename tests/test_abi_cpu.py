@@ -78,7 +78,7 @@ def test_argument_checks_precede_device_work(dl):
         dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), variant=6)
     assert e.value.code == dl.DIR_EINVAL
     with pytest.raises(dl.DirError) as e:
-        dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), image_dtype=dl.DIR_I16)
+        dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), image_dtype=dl.DIR_F16)
     assert e.value.code == dl.DIR_EUNSUPPORTED
     for bad in (dict(levels=0), dict(levels=9), dict(sigma=0.0), dict(sigma=3.0),
                 dict(stop_mode=1, stop_window=0), dict(iters=[-1, 1, 1])):

@@ -1,0 +1,120 @@
+"""Batched registrations (one captured graph over many contexts) and the
+launch-shape autotuner.
+
+A registration's field does not depend on how its kernels are grouped or
+shaped: the batch runs the same kernels as a plain dir_register, only on
+concurrent graph branches, and the autotuner changes only how many voxels a
+thread or block covers, never the arithmetic of a voxel.  So fields are
+compared exactly with plain single registrations, which the parity tests hold
+against the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_0909_0928_gb300 as dl
+    return dl
+
+
+# uneven pairs: (dims, variant, image dtype)
+CASES = [((48, 40, 24), 0, "f32"), ((64, 48, 32), 5, "i16"), ((40, 40, 40), 5, "f32"),
+         ((72, 56, 20), 0, "i16"), ((96, 80, 36), 0, "f32"), ((33, 45, 27), 5, "f32"),
+         ((128, 96, 48), 5, "i16")]
+
+
+def _pair(k, dims, dtype):
+    from phantom import make_blob_pair
+    S, M = make_blob_pair(dims, (1.0, -0.5, 0.5), seed=40 + k, n_blobs=20, sigma_vox=3.0,
+                          noise=0.5)
+    if dtype == "i16":  # integer intensities, stored as int16
+        return (np.round(S * 100).astype(np.int16), np.round(M * 100).astype(np.int16))
+    return S, M
+
+
+def _ctx(dl, S, M, variant, iters=(20, 12, 8)):
+    nz, ny, nx = S.shape
+    params = dl.dir_params_default(levels=3, iters=list(iters))
+    St, Mt = torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda()
+    dt = dl.DIR_I16 if S.dtype == np.int16 else dl.DIR_F32
+    return dl.dir_create(St, Mt, (nx, ny, nz), (1.0, 1.0, 2.0), dt, True, variant, params,
+                         torch.cuda.current_stream())
+
+
+def _field(dl, ctx, shape):
+    out = np.empty((3,) + shape, np.float32)
+    dl.dir_get_field(ctx, out)
+    return out
+
+
+def test_batch_equals_plain_registrations(dl):
+    pairs = [_pair(k, d, t) for k, (d, _, t) in enumerate(CASES)]
+    plain = []
+    for (S, M), (_, v, _) in zip(pairs, CASES):
+        ctx = _ctx(dl, S, M, v)
+        try:
+            dl.dir_register(ctx)
+            plain.append(_field(dl, ctx, S.shape))
+        finally:
+            dl.dir_destroy(ctx)
+    ctxs = [_ctx(dl, S, M, v) for (S, M), (_, v, _) in zip(pairs, CASES)]
+    batch = None
+    try:
+        for branches in (3, 8):
+            batch = dl.dir_batch_create(ctxs, branches=branches,
+                                        stream=torch.cuda.current_stream())
+            for rep in range(2):  # a replay gives the same fields again
+                ms = dl.dir_batch_run(batch)
+                assert ms > 0.0
+                for k, ctx in enumerate(ctxs):
+                    f = _field(dl, ctx, pairs[k][0].shape)
+                    assert np.array_equal(f, plain[k]), f"pair {k} branches {branches} rep {rep}"
+                    h = dl.dir_get_history(ctx, 40)
+                    assert h.shape[0] == 40 and np.all(np.isfinite(h[:, 0]))
+            dl.dir_batch_destroy(batch)
+            batch = None
+        # contexts stay usable on their own after the batch is gone
+        dl.dir_register(ctxs[0])
+        assert np.array_equal(_field(dl, ctxs[0], pairs[0][0].shape), plain[0])
+    finally:
+        dl.dir_batch_destroy(batch)
+        for c in ctxs:
+            dl.dir_destroy(c)
+
+
+def test_batch_argument_errors(dl):
+    S, M = _pair(0, (32, 24, 16), "f32")
+    c = _ctx(dl, S, M, 0, iters=(2, 2, 2))
+    try:
+        with pytest.raises(dl.DirError):
+            dl.dir_batch_create([c, c])           # the same context twice
+        with pytest.raises(dl.DirError):
+            dl.dir_batch_create([c], branches=0)
+        with pytest.raises(dl.DirError):
+            dl.dir_autotune(c)                    # needs a finished registration first
+    finally:
+        dl.dir_destroy(c)
+
+
+@pytest.mark.parametrize("variant", [0, 5])
+def test_autotune_keeps_the_field(dl, variant):
+    S, M = _pair(3, (120, 100, 40), "f32")
+    ctx = _ctx(dl, S, M, variant, iters=(15, 10, 6))
+    try:
+        dl.dir_register(ctx)
+        before = _field(dl, ctx, S.shape)
+        shapes = dl.dir_autotune(ctx, reps=3, levels=3)
+        for depth, zc in shapes:
+            assert depth in (1, 2, 4, 8) and zc >= 0
+        after_tune = _field(dl, ctx, S.shape)     # the registered field is kept
+        assert np.array_equal(after_tune, before)
+        dl.dir_register(ctx)                      # re-captured with the tuned shapes
+        assert np.array_equal(_field(dl, ctx, S.shape), before)
+    finally:
+        dl.dir_destroy(ctx)
