@@ -201,6 +201,9 @@ def ic_field(h) -> np.ndarray:
     return out
 
 
+ROUND32 = 0xFFFFFFFFFFFFFFFF  # probe_seed: single-precision storage of the state
+
+
 def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: float = 1.0,
              alpha: float = 0.4, stop_mode: int = 0, eps: float = 1e-4, stop_window: int = 10,
              init=None, threaded: bool = True, return_raw: bool = False,
@@ -212,6 +215,9 @@ def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: 
     probe_rel > 0 injects relative noise of that size into the warped images
     and the smoothed field every iteration (keyed by probe_seed): a probe of
     how strongly the iteration amplifies rounding, not part of the method.
+    probe_seed = ROUND32 (with any probe_rel > 0) instead stores the state in
+    single precision (pyramid images, the field before and after smoothing and
+    after upsampling, the warped images relative to S).
     """
     S = _f64(S)
     M = _f64(M)
@@ -227,7 +233,7 @@ def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: 
                                     float(sigma), int(levels), it, int(stop_mode), float(eps),
                                     int(stop_window), _p(ini) if ini is not None else None,
                                     _p(u), _p(stats), run, _p(raw) if raw is not None else None,
-                                    float(probe_rel), int(probe_seed))
+                                    float(probe_rel), int(probe_seed) & 0xFFFFFFFFFFFFFFFF)
     if rc != 0:
         raise ValueError(f"or_register failed: {rc}")
     runs = [int(run[i]) for i in range(levels)]

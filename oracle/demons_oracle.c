@@ -338,7 +338,18 @@ static struct {
     double rel;
     uint64_t key;
     int coherent;
-} probe_now = {0.0, 0, 0};
+    int round32; /* store the state in single precision instead of adding noise */
+} probe_now = {0.0, 0, 0, 0};
+
+#define OR_PROBE_ROUND32 0xFFFFFFFFFFFFFFFFull /* probe_seed selecting round32 */
+
+/* Single-precision storage of a state array (round-to-nearest), optionally
+   relative to a reference array: a <- ref + (float)(a - ref). */
+static void probe_round(double* a, const double* ref, size_t n) {
+    if (probe_now.rel == 0.0 || !probe_now.round32) return;
+    for (size_t c = 0; c < n; ++c)
+        a[c] = ref ? ref[c] + (double)(float)(a[c] - ref[c]) : (double)(float)a[c];
+}
 
 static uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -347,7 +358,7 @@ static uint64_t mix64(uint64_t z) {
 }
 
 static void probe_perturb(double* a, size_t n, uint64_t which) {
-    if (probe_now.rel == 0.0) return;
+    if (probe_now.rel == 0.0 || probe_now.round32) return;
     if (probe_now.coherent) {  /* the same relative nudge everywhere */
         for (size_t c = 0; c < n; ++c) a[c] *= 1.0 + probe_now.rel;
         return;
@@ -394,6 +405,8 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     if (ic) or_warp(S, ux, uy, uz, nx, ny, nz, -1.0, Ws);
     probe_perturb(W, n, 1);
     if (ic) probe_perturb(Ws, n, 2);
+    probe_round(W, S, n);
+    if (ic) probe_round(Ws, S, n);
 
     /* gradient of the deformed image(s), recomputed every iteration (Sec. 2.2) */
     if (uses_gm) {
@@ -442,6 +455,10 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     }
     free(part);
 
+    probe_round(vx, NULL, n);
+    probe_round(vy, NULL, n);
+    probe_round(vz, NULL, n);
+
     /* low-pass filter: the total field is smoothed (Thirion, Sec. 2.1) */
     int rc = or_gauss3(vx, ux, nx, ny, nz, sigma);
     rc |= or_gauss3(vy, uy, nx, ny, nz, sigma);
@@ -449,6 +466,9 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     probe_perturb(ux, n, 3);
     probe_perturb(uy, n, 4);
     probe_perturb(uz, n, 5);
+    probe_round(ux, NULL, n);
+    probe_round(uy, NULL, n);
+    probe_round(uz, NULL, n);
     return rc ? -3 : 0;
 }
 
@@ -501,7 +521,11 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /*                2^-53 double rounding                                       */
 /*   probe_seed   key of the probe's hash; 0 makes the probe coherent: every   */
 /*                value is scaled by (1 + probe_rel), the spatially correlated  */
-/*                kind of rounding a smooth field undergoes                     */
+/*                kind of rounding a smooth field undergoes; all ones          */
+/*                (OR_PROBE_ROUND32) instead stores the state in single        */
+/*                precision: coarse pyramid images, the field before and after */
+/*                each smoothing and after upsampling, and the warped images   */
+/*                relative to S (W <- S + float(W - S))                        */
 /* Returns 0 or a negative code.                                              */
 /* ------------------------------------------------------------------------- */
 OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, int nz,
@@ -535,6 +559,8 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
         memcpy(Sl[0], S0, n0 * sizeof(double));
         memcpy(Ml[0], M0, n0 * sizeof(double));
     }
+    probe_now.rel = probe_rel;
+    probe_now.round32 = (probe_rel != 0.0 && probe_seed == OR_PROBE_ROUND32);
     for (int l = 1; l < levels && !rc; ++l) {
         size_t nl = (size_t)dims[l][0] * dims[l][1] * dims[l][2];
         Sl[l] = (double*)malloc(nl * sizeof(double));
@@ -546,6 +572,10 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
         rc = or_downsample(Sl[l - 1], dims[l - 1][0], dims[l - 1][1], dims[l - 1][2], Sl[l]);
         if (!rc)
             rc = or_downsample(Ml[l - 1], dims[l - 1][0], dims[l - 1][1], dims[l - 1][2], Ml[l]);
+        if (!rc) {
+            probe_round(Sl[l], NULL, nl);
+            probe_round(Ml[l], NULL, nl);
+        }
     }
 
     /* field buffers sized for level 0 are reused at every level */
@@ -578,6 +608,7 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
             or_upsample(uprev, px, py, pz, ux, cx, cy, cz);
             or_upsample(uprev + np, px, py, pz, uy, cx, cy, cz);
             or_upsample(uprev + 2 * np, px, py, pz, uz, cx, cy, cz);
+            probe_round(u, NULL, 3 * nl);
         }
         /* per-level constants: grad S (Sec. 2.1) and |grad M| (Eq. 2) */
         double *gsx = g, *gsy = g + nl, *gsz = g + 2 * nl, *bm = g + 3 * nl;
@@ -626,6 +657,7 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
         }
     }
     probe_now.rel = 0.0;
+    probe_now.round32 = 0;
     for (int l = 0; l < levels; ++l) {
         free(Sl[l]);
         free(Ml[l]);

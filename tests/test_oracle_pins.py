@@ -396,3 +396,30 @@ def test_conditioning_of_the_iteration(small_phantom):
     assert sens[3].max() > 1e-3
     worst = np.unravel_index(np.argmax(sens[3]), sens[3].shape)
     assert worst[0] in (0, 1, 2, 29, 30, 31)  # a boundary slab in z
+
+
+def test_single_precision_state_probe(small_phantom):
+    # The ROUND32 probe keeps the method's arithmetic in FP64 but stores its
+    # state in single precision.  Zero stays exactly zero (equal images), a
+    # zero probe size switches it off, and on the passive 50-iteration run it
+    # moves the result by more than nothing but far less than the 1e-3 bar,
+    # while the double force (Eq. 4) is sensitive to it beyond the bar.
+    p = small_phantom
+    S, M = p["S"].astype(np.float64), p["M"].astype(np.float64)
+    z = oracle.register(S, S, variant=3, levels=2, iters=[5, 5], probe_rel=1.0,
+                        probe_seed=oracle.ROUND32)
+    assert np.all(z["u"] == 0.0)
+    plain = oracle.register(S, M, variant=0, levels=1, iters=[50])["u"]
+    off = oracle.register(S, M, variant=0, levels=1, iters=[50], probe_rel=0.0,
+                          probe_seed=oracle.ROUND32)["u"]
+    assert np.array_equal(plain, off)
+    r = oracle.register(S, M, variant=0, levels=1, iters=[50], probe_rel=1.0,
+                        probe_seed=oracle.ROUND32)["u"]
+    d = np.abs(r - plain).max()
+    assert 0.0 < d < 1e-5
+    # the stored field is float-representable after every iteration
+    assert np.array_equal(r, r.astype(np.float32).astype(np.float64))
+    a = oracle.register(S, M, variant=3, levels=1, iters=[50])["u"]
+    b = oracle.register(S, M, variant=3, levels=1, iters=[50], probe_rel=1.0,
+                        probe_seed=oracle.ROUND32)["u"]
+    assert np.abs(a - b).max() > 1e-3
