@@ -10,6 +10,7 @@ second of device time) with s per registration p50/p99 beside it.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--variant passive]
   python bench.py --impl reference   # FP64 CPU oracle on the host cores
   python bench.py --form batch       # 32 uneven int16 pairs: one graph vs 32 plain runs
+  python bench.py --form study       # landmark accuracy per force law, alpha sweep, stop test
 
 Prints one JSON line on rank 0.
 """
@@ -295,6 +296,61 @@ def run_batch(args):
     return 0 if same else 1
 
 
+
+def landmark_error_mm(u_vox, landmarks, u_true_mm, spacing):
+    """Trilinear field at the landmark voxel positions (x, y, z), in mm, against
+    the known field: mean and SD of the 3-D error (the form of Table 3)."""
+    import numpy as np
+    from scipy.ndimage import map_coordinates
+    coords = np.stack([landmarks[:, 2], landmarks[:, 1], landmarks[:, 0]])  # (z, y, x)
+    ue = np.stack([map_coordinates(u_vox[c], coords, order=1, mode="nearest")
+                   for c in range(3)], 1) * np.asarray(spacing)
+    err = np.linalg.norm(ue - u_true_mm, axis=1)
+    return float(err.mean()), float(err.std())
+
+
+def run_study(args):
+    """Accuracy studies on the full-size phantom with its known deformation
+    (Sec. 3.2 evaluation on synthetic landmarks): every force law, the alpha
+    of Eq. (5) from 0.1 to 5, and the relative-norm stop test of Sec. 2.4."""
+    import numpy as np
+    import torch
+    import paper_0909_0928_gb300 as dl
+    from phantom import FULL, make_lung_phantom
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    ph = make_lung_phantom(FULL)
+    S_d, M_d = torch.from_numpy(ph["S"]).cuda(), torch.from_numpy(ph["M"]).cuda()
+    lm, ut = ph["landmarks"], ph["u_true_mm"]
+    init = np.linalg.norm(ut, axis=1)
+    out = {"mode": "study", "workload": workload_config(0, 0.4, 1)["workload"],
+           "landmarks": int(lm.shape[0]),
+           "initial_mm": {"mean": float(init.mean()), "sd": float(init.std())}}
+
+    def run(variant, alpha=0.4, stop_mode=0, eps=1e-4):
+        p = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, stop_mode=stop_mode,
+                                  eps=eps, stop_window=10)
+        ctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, variant, p, stream)
+        try:
+            st = dl.dir_register(ctx)
+            ms = [dl.dir_register(ctx).ms_total for _ in range(3)]
+            u = np.empty((3,) + ph["S"].shape, np.float32)
+            dl.dir_get_field(ctx, u)
+        finally:
+            dl.dir_destroy(ctx)
+        m, sd = landmark_error_mm(u, lm, ut, SPACING)
+        return {"landmark_mm": {"mean": m, "sd": sd}, "ms": statistics.median(ms),
+                "iters_run": list(st.iters_run[:LEVELS]), "mse_final": st.mse_final}
+
+    out["variants"] = {VARIANT_NAMES[v]: run(v) for v in range(6)}
+    out["alpha_sweep_adjusted_double"] = {str(a): run(4, alpha=a)
+                                          for a in (0.1, 0.2, 0.4, 1.0, 2.0, 5.0)}
+    out["stop_test_passive"] = {f"{e:g}": run(0, stop_mode=1, eps=e)
+                                for e in (1e-2, 1e-3, 1e-4, 1e-5)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,7 +361,7 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batch", "study"])
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
@@ -314,6 +370,8 @@ def main():
         return run_reference(args)
     if args.form == "batch":
         return run_batch(args)
+    if args.form == "study":
+        return run_study(args)
 
     import numpy as np
     import torch

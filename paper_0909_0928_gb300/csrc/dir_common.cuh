@@ -188,6 +188,37 @@ __device__ __forceinline__ void block_reduce3_atomic(Real a, Real b, Real c, dou
     }
 }
 
+// ------------------------------------------------- packed single precision
+// Two float lanes in one 64-bit register (low lane = first float in memory),
+// operated on by the f32x2 instructions of sm_100 and later: one instruction
+// does two independent single-precision operations, each rounded exactly as
+// its scalar counterpart.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {  // a * b + c
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // ---------------------------------------------------------------- TMA / mbarrier
 // Bulk tensor copies (cp.async.bulk.tensor) complete on an mbarrier in shared
 // memory; waits are bounded by the global timer so that a copy that never
@@ -234,12 +265,28 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete is
+// suspended in hardware until it completes (or the hint runs out) instead of
+// re-issuing the test, so a waiting warp takes no issue slots from the others.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity,
+                                                      uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Waits for phase `parity` of the barrier; gives up after limit_ns.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_suspend(bar, parity, 1000000u)) {
         if (global_ns() - t0 > limit_ns) return false;
     }
     return true;

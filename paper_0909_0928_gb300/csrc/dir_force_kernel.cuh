@@ -37,6 +37,66 @@ namespace dirk {
 constexpr int FTX = 32, FTY = 8, FNT = FTX * FTY;
 constexpr int HX = FTX + 2, HY = FTY + 2;
 
+
+// Interpolation constants of one level for the force kernel's gathers (Sec. 2.5
+// software trilinear, clamped): the upper corner is one element to the right
+// along x and sy / sz elements further along y / z, with sy or sz 0 on an axis
+// of one voxel.  On an x axis of one voxel the weight of the right neighbour is
+// 0 and that neighbour is row padding (zero in the image pool), so the read is
+// harmless.
+struct Interp {
+    int nx1, ny1, nz1;     // n - 1
+    int nxm2, nym2, nzm2;  // max(n - 2, 0): largest lower corner
+    int px, pl, sy, sz;
+    __device__ __forceinline__ explicit Interp(const Grid3& g)
+        : nx1(g.nx - 1), ny1(g.ny - 1), nz1(g.nz - 1), nxm2(max(g.nx - 2, 0)),
+          nym2(max(g.ny - 2, 0)), nzm2(max(g.nz - 2, 0)), px(g.px), pl((int)g.plane),
+          sy(g.ny > 1 ? g.px : 0), sz(g.nz > 1 ? (int)g.plane : 0) {}
+};
+
+// Lower corner and weight along one axis at p = base + off: p clamped to
+// [0, n-1] in offset form (exact: the bounds are small integers), corner
+// floor(p) kept <= n-2 (weight 1 at the upper clamp).
+template <typename Real>
+__device__ __forceinline__ int ax_corner(int base, Real off, int nm1, int nm2, Real& f) {
+    const Real c = r_clamp(off, Real(-base), Real(nm1 - base));
+    const Real fl = r_floor(c);
+    int i = base + (int)fl;
+    f = c - fl;
+    if (i > nm2) {
+        i = nm2;
+        f = Real(1);
+    }
+    return i;
+}
+
+// I(x + o) - ref, corners taken relative to ref (see trilinear in
+// dir_common.cuh for why), lerped along x, then y, then z.
+template <typename Real, typename T>
+__device__ __forceinline__ Real interp_rel(const T* __restrict__ I, const Interp& q, int x, Real ox,
+                                           int y, Real oy, int z, Real oz, Real ref) {
+    Real fx, fy, fz;
+    const int ix = ax_corner(x, ox, q.nx1, q.nxm2, fx);
+    const int iy = ax_corner(y, oy, q.ny1, q.nym2, fy);
+    const int iz = ax_corner(z, oz, q.nz1, q.nzm2, fz);
+    const T* p0 = I + (ix + q.px * iy + q.pl * iz);
+    const T* p1 = p0 + q.sy;
+    const T* p2 = p0 + q.sz;
+    const T* p3 = p2 + q.sy;
+    const Real c000 = ldg_as<Real>(p0) - ref, c100 = ldg_as<Real>(p0 + 1) - ref;
+    const Real c010 = ldg_as<Real>(p1) - ref, c110 = ldg_as<Real>(p1 + 1) - ref;
+    const Real c001 = ldg_as<Real>(p2) - ref, c101 = ldg_as<Real>(p2 + 1) - ref;
+    const Real c011 = ldg_as<Real>(p3) - ref, c111 = ldg_as<Real>(p3 + 1) - ref;
+    const Real gx = Real(1) - fx, gy = Real(1) - fy, gz = Real(1) - fz;
+    const Real v00 = c000 * gx + c100 * fx;
+    const Real v10 = c010 * gx + c110 * fx;
+    const Real v01 = c001 * gx + c101 * fx;
+    const Real v11 = c011 * gx + c111 * fx;
+    const Real v0 = v00 * gy + v10 * fy;
+    const Real v1 = v01 * gy + v11 * fy;
+    return v0 * gz + v1 * fz;
+}
+
 template <int V>
 struct VT {
     static constexpr bool GM = (V == 2 || V == 3 || V == 4 || V == 5);  // warped gradient
@@ -64,6 +124,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     const int xm = max(xc - 1, 0), xp = min(xc + 1, g.nx - 1);
     const int ym = max(yc - 1, 0), yp = min(yc + 1, g.ny - 1);
     const int cs = (int)g.cs;
+    const Interp ip(g);
 
     // D = W - S (Eq. 6: D_m + D_s with D_m = W_m - S, D_s = W_s - S) on the brick
     // plus halo; Eq. 6 also d = D_m - D_s on the brick
@@ -81,9 +142,9 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
             const int o = offs(g, gx, gy, gz);
             const Real ux = ldg_as<Real>(u + o), uy = ldg_as<Real>(u + o + cs), uz = ldg_as<Real>(u + o + 2 * cs);
             const Real sref = ldg_as<Real>(S + o);
-            const Real wm = trilinear(M, g, gx, ux, gy, uy, gz, uz, sref);
+            const Real wm = interp_rel(M, ip, gx, ux, gy, uy, gz, uz, sref);
             if (T::IC) {
-                const Real ws = trilinear(S, g, gx, -ux, gy, -uy, gz, -uz, sref);
+                const Real ws = interp_rel(S, ip, gx, -ux, gy, -uy, gz, -uz, sref);
                 Wt[hz][hy][hx] = wm + ws;
                 if (hx >= 1 && hx <= FTX && hy >= 1 && hy <= FTY && hz >= 1 && hz <= FTZ)
                     Dt[T::IC ? hz - 1 : 0][hy - 1][hx - 1] = wm - ws;
@@ -142,7 +203,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
                     else
                         d = Wt[k + 1][ty + 1][tx + 1];
                 } else {
-                    d = trilinear(M, g, x, ux, y, uy, z, uz, scol[k + 1]);
+                    d = interp_rel(M, ip, x, ux, y, uy, z, uz, scol[k + 1]);
                 }
                 Real dx, dy, dz;
                 demons_force<Real, V>(d, gsx, gsy, gsz, gmx, gmy, gmz, bm, alpha2, dx, dy, dz);

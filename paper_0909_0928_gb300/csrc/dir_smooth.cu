@@ -66,6 +66,273 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8, TIN>::YT)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Single-precision field smoothing, packed.  A block of 128 threads smooths
+// one component of a 32 x 16 (x, y) tile over a z chunk.  Each input plane
+// (tile + halo, H = 16 + 2R rows) arrives by TMA into a 4-slot ring; the x
+// pass (scalar, 4 outputs per task from 128-bit shared loads) writes its rows
+// into a pair-interleaved buffer in which row m sits beside row m + 8, so that
+// the y and z passes run on f32x2 pairs (rows y and y + 8 of one column): a
+// thread owns column lx and rows {2q, 2q+1, 2q+8, 2q+9}, filters them in y
+// from 64-bit shared loads, keeps the 2R+1 most recent y-filtered planes in
+// registers and filters them in z.  The y and z passes are instantiated for
+// each ring position (a switch on the plane index modulo 2R+1), so the
+// register ring rotates by renaming, not by moves, without unrolling the
+// whole plane loop.
+// ---------------------------------------------------------------------------
+constexpr int S2X = 32, S2Y = 16, S2T = 128, S2STAGES = 6;
+constexpr int S2TP = S2X + 1;  // pair-row pitch in f32x2 (the pad staggers banks)
+
+template <int R>
+struct S2Geom {
+    static constexpr int K = 2 * R + 1;
+    static constexpr int H = S2Y + 2 * R;                // box rows
+    static constexpr int HA = (R + 3) / 4 * 4;           // x halo: TMA x start 16-byte aligned
+    static constexpr int WB = S2X + 2 * HA;              // box width
+    static constexpr int NPR = S2Y / 2 + 2 * R;          // pair rows (m, m + 8)
+    static constexpr int XLV = (HA - R + 4 + 2 * R + 3) / 4 * 4;  // x-task inputs, whole float4s
+    static constexpr int SLOT = H * WB * 4;              // bytes per stage
+    static constexpr int SLOT_STRIDE = (SLOT + 127) / 128 * 128;
+    static constexpr int TXP = NPR * S2TP * 8;
+    static constexpr int SMEM = 128 + S2STAGES * SLOT_STRIDE + (TXP + 127) / 128 * 128 + 64;
+};
+
+
+// y pass of one plane into ring slot J, then (once 2R+1 planes are in) the z
+// pass over the ring, oldest plane first, and the stores of output plane zo
+template <int R, int J>
+__device__ __forceinline__ void s2_yz(const f32x2* __restrict__ txp, int q, int lx,
+                                      const f32x2 (&wp)[R + 1], f32x2 (&ring)[2 * R + 1][2],
+                                      bool emit, float* __restrict__ o, int px, int rows_left) {
+    constexpr int K = 2 * R + 1;  // taps are symmetric: tap t is wp[min(t, 2R - t)]
+    f32x2 in2[K + 1];
+#pragma unroll
+    for (int m = 0; m < K + 1; ++m) in2[m] = txp[(2 * q + m) * S2TP + lx];
+    f32x2 p0 = 0ull, p1 = 0ull;
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p0 = f2_fma(wp[t <= R ? t : 2 * R - t], in2[t], p0);
+        p1 = f2_fma(wp[t <= R ? t : 2 * R - t], in2[t + 1], p1);
+    }
+    ring[J][0] = p0;
+    ring[J][1] = p1;
+    if (emit) {
+        f32x2 r0 = 0ull, r1 = 0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            r0 = f2_fma(wp[t <= R ? t : 2 * R - t], ring[(J + 1 + t) % K][0], r0);
+            r1 = f2_fma(wp[t <= R ? t : 2 * R - t], ring[(J + 1 + t) % K][1], r1);
+        }
+        float a0, b0, a1, b1;
+        f2_unpack(r0, a0, b0);
+        f2_unpack(r1, a1, b1);
+        // rows ya, ya + 1, ya + 8, ya + 9; rows_left = ny - ya (x checked by the caller)
+        if (rows_left > 0) o[0] = a0;
+        if (rows_left > 1) o[px] = a1;
+        if (rows_left > S2Y / 2) o[(S2Y / 2) * px] = b0;
+        if (rows_left > S2Y / 2 + 1) o[(S2Y / 2 + 1) * px] = b1;
+    }
+}
+
+
+// x pass of one task: box row rho, outputs 4 gq .. 4 gq + 3, written to the
+// pair rows (rho as the upper lane of pair row rho, the lower lane of pair
+// row rho - 8)
+template <int R>
+__device__ __forceinline__ void s2_xtask(const float* __restrict__ slot, float* __restrict__ txf,
+                                         int tk, const float (&w)[R + 1]) {
+    using G = S2Geom<R>;
+    constexpr int K = 2 * R + 1, HA = G::HA, WB = G::WB, NPR = G::NPR;
+    const int gq = tk & 7, rho = tk >> 3;
+    const float* src = slot + rho * WB + 4 * gq;
+    float in[G::XLV];
+#pragma unroll
+    for (int v = 0; v < G::XLV / 4; ++v) {
+        const float4 t4 = reinterpret_cast<const float4*>(src)[v];
+        in[4 * v] = t4.x;
+        in[4 * v + 1] = t4.y;
+        in[4 * v + 2] = t4.z;
+        in[4 * v + 3] = t4.w;
+    }
+    float o[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < K; ++t) acc = fmaf(w[t <= R ? t : 2 * R - t], in[HA - R + jj + t], acc);
+        o[jj] = acc;
+    }
+    if (rho < NPR) {
+        float* d = txf + 2 * (rho * S2TP + 4 * gq);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
+    }
+    if (rho >= S2Y / 2) {
+        float* d = txf + 2 * ((rho - S2Y / 2) * S2TP + 4 * gq) + 1;
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(S2T, 8)
+    smooth2_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    using G = S2Geom<R>;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB, NPR = G::NPR;
+    extern __shared__ unsigned char smem_raw[];
+    // 128-byte aligned, by pointer arithmetic on the shared array (keeps the
+    // accesses below in the shared address space)
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    f32x2* txp = reinterpret_cast<f32x2*>(base + S2STAGES * G::SLOT_STRIDE);
+    float* txf = reinterpret_cast<float*>(txp);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S2STAGES * G::SLOT_STRIDE +
+                                                 (G::TXP + 127) / 128 * 128);
+    const Grid3 g = a.g;
+    float w[R + 1];  // symmetric taps: w[t] for t = 0..R (outermost first)
+    f32x2 wp[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+        w[t] = a.taps.wf[t];
+        wp[t] = f2_pack(w[t], w[t]);
+    }
+    const int tid = threadIdx.x;
+    const int lx = tid & 31, q = tid >> 5;
+    const int comp = blockIdx.z % a.ncomp;
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * S2Y;
+    const int z0 = (blockIdx.z / a.ncomp) * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const int nsteps = (z1 - z0) + 2 * R;  // input planes z0-R .. z1-1+R (clamped)
+    const int bx = x0 - HA, by = y0 - R;
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
+    float* __restrict__ out = static_cast<float*>(a.out) + (long long)comp * g.cs;
+
+    auto issue = [&](int step) {
+        const int sl = step % S2STAGES;
+        const int pc = clampi(z0 - R + step, 0, g.nz - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
+        tma_load_4d(base + sl * G::SLOT_STRIDE, &tmap, bx, by, pc, comp, &full[sl]);
+    };
+    if (tid == 0) {
+        for (int sl = 0; sl < S2STAGES; ++sl) mbar_init(&full[sl], 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        for (int st = 0; st < S2STAGES - 1 && st < nsteps; ++st) issue(st);
+    }
+    __syncthreads();
+
+    f32x2 ring[K][2];
+#pragma unroll
+    for (int t = 0; t < K; ++t) ring[t][0] = ring[t][1] = 0ull;
+
+    const int x = x0 + lx;
+    const int ya = y0 + 2 * q;  // rows ya, ya + 1 (lane 0) and ya + 8, ya + 9 (lane 1)
+    const int px = (int)g.px;
+    const int rows_left = x < g.nx ? g.ny - ya : 0;  // 0: this thread stores nothing
+    for (int step = 0; step < nsteps; ++step) {
+        if (tid == 0 && step + S2STAGES - 1 < nsteps) issue(step + S2STAGES - 1);
+        const int sl = step % S2STAGES;
+        const uint32_t parity = (uint32_t)((step / S2STAGES) & 1);
+        bool ok = true;
+        if (tid == 0) ok = mbar_wait_bounded(&full[sl], parity, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+            return;
+        }
+        (void)mbar_try_wait(&full[sl], parity);
+        float* slot = reinterpret_cast<float*>(base + sl * G::SLOT_STRIDE);  // [H][WB]
+        if (edge) {  // replicate boundary: columns per row, then rows per column
+            const int lo = max(0, -bx), hi = min(WB, g.nx - bx);
+            for (int row = tid; row < H; row += S2T) {
+                float* r = slot + row * WB;
+                const float left = r[lo], right = r[hi - 1];
+                for (int hx = 0; hx < lo; ++hx) r[hx] = left;
+                for (int hx = hi; hx < WB; ++hx) r[hx] = right;
+            }
+            __syncthreads();
+            const int rlo = max(0, -by), rhi = min(H, g.ny - by);
+            for (int col = tid; col < WB; col += S2T) {
+                float* c = slot + col;
+                const float top = c[rlo * WB], bot = c[(rhi - 1) * WB];
+                for (int hy = 0; hy < rlo; ++hy) c[hy * WB] = top;
+                for (int hy = rhi; hy < H; ++hy) c[hy * WB] = bot;
+            }
+            __syncthreads();
+        }
+        // x pass: H * 8 tasks (between 128 and 256 for R = 1..4)
+        static_assert(H * (S2X / 4) > S2T && H * (S2X / 4) <= 2 * S2T, "x tasks per thread");
+        s2_xtask<R>(slot, txf, tid, w);
+        if (tid < H * (S2X / 4) - S2T) s2_xtask<R>(slot, txf, tid + S2T, w);
+        __syncthreads();
+        const bool emit = step >= 2 * R;
+        float* o = out + offs(g, x < g.nx ? x : 0, ya, emit ? z0 + step - 2 * R : 0);
+        switch (step % K) {
+#define S2_CASE(J)                                                          \
+    case J:                                                                 \
+        if constexpr (J < K) s2_yz<R, J>(txp, q, lx, wp, ring, emit, o, px, rows_left); \
+        break;
+            S2_CASE(0) S2_CASE(1) S2_CASE(2) S2_CASE(3) S2_CASE(4) S2_CASE(5) S2_CASE(6)
+            S2_CASE(7) S2_CASE(8)
+#undef S2_CASE
+        }
+        // no barrier here: the next step's __syncthreads_or orders this
+        // step's reads of the pair rows before the next x pass rewrites them
+    }
+}
+
+template <int R>
+static bool make_s2_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
+    using G = S2Geom<R>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
+                                (cuuint64_t)ncomp};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                   (cuuint64_t)g.cs * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// z chunk for the packed kernel: the largest number of chunks that still fits
+// in one wave of resident blocks
+static int s2_zchunk(const Grid3& g, int per_sm, int num_sms, int ncomp) {
+    if (per_sm < 1) per_sm = 1;
+    const long long bxy = (long long)((g.nx + S2X - 1) / S2X) * ((g.ny + S2Y - 1) / S2Y) * ncomp;
+    long long chunks = ((long long)per_sm * num_sms) / bxy;
+    if (chunks < 1) chunks = 1;
+    if (chunks > g.nz) chunks = g.nz;
+    const int zc = (int)((g.nz + chunks - 1) / chunks);
+    return zc < 1 ? 1 : zc;
+}
+
+template <int R>
+static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    using G = S2Geom<R>;
+    CUtensorMap map;
+    if (!make_s2_map<R>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    static int per_sm = 1;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(smooth2_kernel<R>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth2_kernel<R>, S2T, G::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int zc = a.zchunk > 0 ? a.zchunk : s2_zchunk(a.g, per_sm, num_sms, a.ncomp);
+    if (zc > a.g.nz) zc = a.g.nz;
+    const int chunks = (a.g.nz + zc - 1) / zc;
+    const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + S2Y - 1) / S2Y, chunks * a.ncomp);
+    smooth2_kernel<R><<<grid, dim3(S2T, 1, 1), G::SMEM, s>>>(map, a, zc);
+    return cudaGetLastError();
+}
+
 template <typename Real, int R, typename TIN, typename TOUT>
 static cudaError_t launch_rt(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     using G = StencilGeom<Real, R, 1, 8, TIN>;
@@ -111,8 +378,15 @@ cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStrea
         if (a.in_type != kStoreF64 || a.out_type != kStoreF64) return cudaErrorInvalidValue;
         return launch_types<double, double, double>(a, num_sms, s);
     }
-    if (a.in_type == kStoreF32 && a.out_type == kStoreF32)
-        return launch_types<float, float, float>(a, num_sms, s);
+    if (a.in_type == kStoreF32 && a.out_type == kStoreF32) {
+        switch (a.taps.R) {  // the packed kernel for the usual radii
+            case 1: return launch_s2<1>(a, num_sms, s);
+            case 2: return launch_s2<2>(a, num_sms, s);
+            case 3: return launch_s2<3>(a, num_sms, s);
+            case 4: return launch_s2<4>(a, num_sms, s);
+            default: return launch_types<float, float, float>(a, num_sms, s);
+        }
+    }
     if (a.in_type == kStoreI16 && a.out_type == kStoreF32)
         return launch_types<float, int16_t, float>(a, num_sms, s);
     if (a.in_type == kStoreBF16 && a.out_type == kStoreBF16)

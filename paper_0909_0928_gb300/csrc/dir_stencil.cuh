@@ -119,8 +119,9 @@ struct PlanePipe {
     __device__ void setup(unsigned char* smem_raw, const Grid3& g, int x0, int y0, int zstart,
                           int zend, int c0 = 0) {
         comp0 = c0;
-        base = reinterpret_cast<unsigned char*>(
-            (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+        // 128-byte aligned by pointer arithmetic on the shared array, so that
+        // the accesses stay in the shared address space
+        base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
         txp = reinterpret_cast<Real*>(base + STAGES * G::SLOT_STRIDE);
         full = reinterpret_cast<uint64_t*>(base + STAGES * G::SLOT_STRIDE + G::TXP_STRIDE);
         z0 = zstart;

@@ -9,6 +9,9 @@ Gaussian of radius ceil(3 sigma) applied x, y, z (Sec. 2.5), du = -dr with the
 forces of Eqs. (1)-(6), total field smoothed (Sec. 2.1), pyramid by Gaussian
 then even samples and fields upsampled as 2 * u(x / 2) (Sec. 2.3).
 Arrays are (nz, ny, nx); fields (3, nz, ny, nx) with components (x, y, z).
+`register(..., dtype=np.float32)` runs the same steps in single precision: an
+independent FP32 implementation whose deviation from the oracle calibrates the
+single-precision parity criterion.
 """
 from __future__ import annotations
 
@@ -27,7 +30,7 @@ def interp(I, px, py, pz):
         lo = np.clip(np.floor(p), 0, max(n - 2, 0)).astype(np.int64)
         hi = np.minimum(lo + 1, n - 1)
         idx.append((lo, hi))
-        wts.append(p - lo)
+        wts.append(p - lo.astype(p.dtype))
     (x0, x1), (y0, y1), (z0, z1) = idx
     fx, fy, fz = wts
     out = 0.0
@@ -49,15 +52,15 @@ def grad(I):
     return g
 
 
-def taps(sigma):
+def taps(sigma, dtype=np.float64):
     R = int(math.ceil(3.0 * sigma))
     t = np.arange(-R, R + 1, dtype=np.float64)
     w = np.exp(-t * t / (2.0 * sigma * sigma))
-    return w / w.sum(), R
+    return (w / w.sum()).astype(dtype), R
 
 
 def gauss3(I, sigma):
-    w, R = taps(sigma)
+    w, R = taps(sigma, I.dtype)
     out = I
     for c in range(3):  # x, then y, then z
         a = AXIS[c]
@@ -74,14 +77,14 @@ def downsample(I):
     return gauss3(I, 1.0)[::2, ::2, ::2].copy()
 
 
-def grid(shape):
+def grid(shape, dtype=np.float64):
     nz, ny, nx = shape
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    return i.astype(np.float64), j.astype(np.float64), k.astype(np.float64)
+    return i.astype(dtype), j.astype(dtype), k.astype(dtype)
 
 
 def upsample(uc, shape):
-    i, j, k = grid(shape)
+    i, j, k = grid(shape, uc.dtype)
     return np.stack([2.0 * interp(uc[c], i / 2.0, j / 2.0, k / 2.0) for c in range(3)])
 
 
@@ -112,7 +115,7 @@ def force(variant, d, gs, gm, b, alpha):
 
 
 def iterate(variant, S, M, u, sigma, alpha, gs, bm):
-    i, j, k = grid(S.shape)
+    i, j, k = grid(S.shape, S.dtype)
     W = interp(M, i + u[0], j + u[1], k + u[2])
     if variant == 5:
         Ws = interp(S, i - u[0], j - u[1], k - u[2])
@@ -128,8 +131,8 @@ def iterate(variant, S, M, u, sigma, alpha, gs, bm):
     return np.stack([gauss3(v[c], sigma) for c in range(3)]), red
 
 
-def register(S, M, variant, levels, iters, sigma=1.0, alpha=0.4):
-    pyr_s, pyr_m = [S.astype(np.float64)], [M.astype(np.float64)]
+def register(S, M, variant, levels, iters, sigma=1.0, alpha=0.4, dtype=np.float64):
+    pyr_s, pyr_m = [S.astype(dtype)], [M.astype(dtype)]
     for _ in range(1, levels):
         pyr_s.append(downsample(pyr_s[-1]))
         pyr_m.append(downsample(pyr_m[-1]))
@@ -138,7 +141,7 @@ def register(S, M, variant, levels, iters, sigma=1.0, alpha=0.4):
     for lc in range(levels):
         lv = levels - 1 - lc
         Sl, Ml = pyr_s[lv], pyr_m[lv]
-        u = np.zeros((3,) + Sl.shape) if u is None else upsample(u, Sl.shape)
+        u = np.zeros((3,) + Sl.shape, dtype) if u is None else upsample(u, Sl.shape)
         gs = grad(Sl)
         bm = np.sqrt(np.sum(grad(Ml) ** 2, axis=0))
         for _ in range(iters[lc]):
@@ -148,7 +151,7 @@ def register(S, M, variant, levels, iters, sigma=1.0, alpha=0.4):
 
 
 def ic_field(h, steps=20):
-    i, j, k = grid(h.shape[1:])
+    i, j, k = grid(h.shape[1:], h.dtype)
     px, py, pz = i.copy(), j.copy(), k.copy()
     for _ in range(steps):
         ax, ay, az = (interp(h[c], px, py, pz) for c in range(3))

@@ -1,4 +1,5 @@
-"""The C oracle against the independent NumPy twin on tiny volumes (<= 16^3)."""
+"""The C oracle against the independent NumPy twin on tiny volumes (<= 16^3), and
+the twin in float32 as a calibration of the single-precision parity criterion."""
 import numpy as np
 import pytest
 
@@ -38,3 +39,46 @@ def test_registration_matches_twin(variant, levels):
     np.testing.assert_allclose(r["stats"], stats, rtol=1e-12, atol=1e-12)
     if variant == 5:
         np.testing.assert_allclose(r["u"], twin.ic_field(u), atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Calibration of the single-precision parity criterion (parity_criteria.py):
+# an independent FP32 implementation of the same steps (this twin in
+# float32, written without the GPU path's care for rounding) must pass it,
+# and the same twin with a plausible slip must not.
+
+def _ragged(dims, seed):
+    from phantom import PhantomSpec, make_lung_phantom
+    spec = PhantomSpec(dims=dims, spacing=(1.2, 1.2, 2.5), seed=seed, a_max_mm=5.0,
+                       compression=0.1, n_vessels=12, n_landmarks=50)
+    p = make_lung_phantom(spec)
+    return p["S"], p["M"]
+
+
+@pytest.mark.parametrize("variant,dims,seed", [(5, (70, 9, 33), 16), (0, (45, 37, 19), 11),
+                                               (2, (45, 37, 19), 13)])
+def test_fp32_twin_passes_the_single_precision_criterion(variant, dims, seed):
+    from parity_criteria import fp32_spread, shadow_check
+    S, M = _ragged(dims, seed)
+    sched = dict(levels=3, iters=[12, 8, 6])
+    ref = oracle.register(S, M, variant=variant, alpha=0.4, **sched)
+    spread = fp32_spread(oracle, S, M, variant, ref_u=ref["u"], **sched)
+    u32, _ = twin.register(S, M, variant, 3, [12, 8, 6], dtype=np.float32)
+    if variant == 5:
+        u32 = twin.ic_field(u32)
+    err = np.abs(u32.astype(np.float64) - ref["u"]).max(axis=0)
+    assert err.max() > 0.0
+    shadow_check(err, spread, 1e-3, f"twin32 v{variant} {dims}")
+
+
+def test_the_criterion_rejects_a_slip():
+    # a smoothing width off by 2% (a plausible slip in the taps) fails it
+    from parity_criteria import fp32_spread, shadow_check
+    S, M = _ragged((45, 37, 19), 11)
+    sched = dict(levels=3, iters=[12, 8, 6])
+    ref = oracle.register(S, M, variant=0, alpha=0.4, **sched)
+    spread = fp32_spread(oracle, S, M, 0, ref_u=ref["u"], **sched)
+    u, _ = twin.register(S, M, 0, 3, [12, 8, 6], sigma=1.02)
+    err = np.abs(u - ref["u"]).max(axis=0)
+    with pytest.raises(AssertionError):
+        shadow_check(err, spread, 1e-3, "slipped twin")
