@@ -50,6 +50,22 @@ def level_dims(dims, levels):
     return out
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (timing rule: max over ranks)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, world: int, max_ms: float) -> float:
+    """Units all ranks processed (replicas: each rank does the same work) per
+    second of the slowest rank's timed region."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
 def voxel_updates(dims, levels, iters):
     lv = level_dims(dims, levels)
     return sum(lv[levels - 1 - lc][0] * lv[levels - 1 - lc][1] * lv[levels - 1 - lc][2] * iters[lc]
@@ -75,19 +91,33 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel: str, src_file: str):
+# source files each timed kernel is built from (its traffic figure in profiles/
+# is valid only while their combined sha256 is unchanged)
+KERNEL_SOURCES = {
+    "force_kernel": ["dir_force_kernel.cuh", "dir_force_law.cuh", "dir_common.cuh"],
+    "smooth2_kernel": ["dir_smooth.cu", "dir_common.cuh"],
+    "fused_kernel": ["dir_fused.cu", "dir_stencil.cuh", "dir_force_law.cuh", "dir_common.cuh"],
+}
+
+
+def sources_sha256(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_0909_0928_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, valid only while
-    the kernel source is unchanged since the capture (sha256 recorded there)."""
-    src = os.path.join(ROOT, "paper_0909_0928_gb300", "csrc", src_file)
+    the kernel's sources are unchanged since the capture (sha256 recorded)."""
     summ = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         vals = {}
         for line in open(summ):
             if ":" in line:
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-        if vals.get("source_sha256") == sha:
+        if vals.get("source_sha256") == sources_sha256(kernel):
             return float(vals["dram_bytes_per_launch_full_size"])
     except Exception:
         pass
@@ -362,6 +392,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--form", default="plain", choices=["plain", "batch", "study"])
+    ap.add_argument("--fuse", type=int, default=0, choices=[0, 1],
+                    help="fold the Gaussian into the next force pass (Eqs. 1-2)")
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
@@ -397,7 +429,8 @@ def main():
     W_d = torch.empty_like(S_d)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    params = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=args.alpha, timing=1)
+    params = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=args.alpha, timing=1,
+                                   fuse=args.fuse)
     ctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, args.variant_id, params, stream)
     vu_step = voxel_updates(DIMS, LEVELS, ITERS)
 
@@ -434,13 +467,11 @@ def main():
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
-    value = world * vu_step * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(vu_step, args.steps, world, total_ms)
 
     # end to end through the public API with host buffers: upload (pinned) ->
     # register -> field download, every step
@@ -466,7 +497,7 @@ def main():
     n_fine = n0
     bytes_pv = {"force": FORCE_BYTES[args.variant_id], "fused": FORCE_BYTES[args.variant_id],
                 "smooth": SMOOTH_BYTES}
-    src_of = {"force": "dir_force.cu", "fused": "dir_fused.cu", "smooth": "dir_smooth.cu"}
+    kernel_of = {"force": "force_kernel", "fused": "fused_kernel", "smooth": "smooth2_kernel"}
     per_kernel = {}
     for k, (ms, n) in kt.items():
         if n:
@@ -476,8 +507,8 @@ def main():
                              "frac": n_fine * bytes_pv[k] / (avg / 1e3) / 1e9 / peak}
     kname = max(per_kernel, key=lambda k: per_kernel[k]["total_ms"])
     kk = per_kernel[kname]
-    traffic = profiled_traffic(kname + "_kernel", src_of[kname])
-    roofline = {"bound": "hbm", "kernel": kname + "_kernel", "achieved": kk["achieved_gbs"],
+    traffic = profiled_traffic(kernel_of[kname])
+    roofline = {"bound": "hbm", "kernel": kernel_of[kname], "achieved": kk["achieved_gbs"],
                 "peak": peak, "unit": "GB/s", "frac": kk["frac"], "traffic": traffic,
                 "algorithmic_bytes_per_launch": n_fine * bytes_pv[kname],
                 "avg_launch_ms": kk["avg_ms"],

@@ -77,7 +77,9 @@ typedef struct {
                                     |l(n) - l(n - stop_window)| <= eps (Sec. 2.4) */
     double eps;                  /* default 1e-4 (Sec. 2.4) */
     int stop_window;             /* default 10 (Sec. 2.4) */
-    dir_dtype field_dtype;       /* DIR_F32 only in this build */
+    dir_dtype field_dtype;       /* storage of the displacement field on the device: DIR_F32
+                                    (default) or DIR_BF16 (half the field bytes, arithmetic
+                                    still FP32; only with precision DIR_F32) */
     const float* init_field;     /* NULL, or a DEVICE pointer to a level-0 field (3*N floats,
                                     voxels) to start from; only with levels == 1 */
     int use_graph;               /* 1 (default): capture the whole registration in a CUDA graph
@@ -88,10 +90,11 @@ typedef struct {
                                     DIR_F32 (default, the production path) or DIR_F64 (the same
                                     kernels in double precision, for verification against an
                                     FP64 reference where the iteration is ill-conditioned) */
-    int fuse;                    /* 1: for Eqs. (1)-(2) without the stop test, fold the Gaussian
-                                    of iteration k into the force pass of iteration k+1 (same
-                                    arithmetic, one pass over the field per iteration);
-                                    0 (default): one force and one smoothing launch per iteration */
+    int fuse;                    /* for Eqs. (1)-(2) without the stop test, with FP32 images and
+                                    field: fold the Gaussian of iteration k into the force pass of
+                                    iteration k+1 (same arithmetic, one pass over the field per
+                                    iteration).  0: never; 1: every level; 2 (default): levels of
+                                    at most 2,000,000 voxels, where it is faster */
 } dir_params;
 
 typedef struct {
@@ -118,9 +121,11 @@ int dir_params_default(dir_params* p);
 
 /*
  * Creates a registration context for one static/moving pair.
- *   static_img, moving_img  dense volumes of image_dtype (DIR_F32 in this build),
- *                           host memory, or device memory if inputs_on_device != 0.
- *                           They are copied; the caller keeps ownership.
+ *   static_img, moving_img  dense volumes of image_dtype: DIR_F32, or DIR_I16 (integer
+ *                           HU, kept as int16 at the finest level, exact; needs
+ *                           precision DIR_F32), host memory, or device memory if
+ *                           inputs_on_device != 0.  They are copied; the caller keeps
+ *                           ownership.
  *   dims                    {nx, ny, nz}, each 1..DIR_MAX_DIM, nx*ny*nz <= DIR_MAX_VOXELS
  *   spacing_mm              voxel size, each > 0 (used only for mm output)
  *   variant                 one of dir_variant

@@ -34,6 +34,11 @@ namespace {
 constexpr int kIcInvertSteps = 20;
 constexpr int kStopUnset = 0x7f7f7f7f;  // memset byte 0x7f
 
+// fuse = 2: levels up to this many voxels use the fused iteration (there the
+// smaller number of launches and passes wins; on larger levels the two-kernel
+// schedule keeps more blocks in flight)
+constexpr long long kFuseAutoVoxels = 2000000;
+
 thread_local std::string g_create_error;
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -297,6 +302,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.alpha2 = c->p.alpha * c->p.alpha;
         fa.stop_iter = c->ctl + lc;
         fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms, 4);
+        fa.pf_stride = 4 * c->num_sms;  // one wave of force blocks (4 per SM)
         fa.img_type = c->img_type(l);
         fa.field_type = c->field_type;
         dirk::SmoothArgs sa;
@@ -310,7 +316,9 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         sa.zchunk = c->tune_zchunk[l];
         const bool timed = c->p.timing && l == 0;
         const int n = c->p.iters[lc];
-        const bool fused = c->p.fuse && c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
+        const long long nvox = (long long)g.nx * g.ny * g.nz;
+        const bool fuse_here = c->p.fuse == 1 || (c->p.fuse == 2 && nvox <= kFuseAutoVoxels);
+        const bool fused = fuse_here && c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
                            c->field_type == c->real_type && c->img_type(l) == c->real_type;
         if (fused && n > 0) {
             // iteration 0 from u, iterations 1..n-1 from the previous v with the
@@ -452,7 +460,7 @@ static int validate_params(const dir_params* p) {
     if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
-    if (p->fuse != 0 && p->fuse != 1) return DIR_EINVAL;
+    if (p->fuse < 0 || p->fuse > 2) return DIR_EINVAL;
     return DIR_OK;
 }
 
@@ -490,7 +498,7 @@ int dir_params_default(dir_params* p) {
     p->use_graph = 1;
     p->timing = 0;
     p->precision = DIR_F32;
-    p->fuse = 0;
+    p->fuse = 2;
     return DIR_OK;
 }
 

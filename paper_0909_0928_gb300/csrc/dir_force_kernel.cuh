@@ -97,6 +97,37 @@ __device__ __forceinline__ Real interp_rel(const T* __restrict__ I, const Interp
     return v0 * gz + v1 * fz;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Prefetch into L2 the rows of the brick that block `b` (linear block index)
+// will read: u (three components) over its FTZ planes, S and M over the planes
+// one below to one above.  Issued for the block one wave ahead, so that its
+// loads of u and S (and M near its voxels) hit L2 instead of HBM.
+template <int FTZ, typename TI, typename TF>
+__device__ __forceinline__ void prefetch_brick(const ForceArgs& a, long long b, int tid, int nt) {
+    const Grid3& g = a.g;
+    const long long gx = gridDim.x, gy = gridDim.y, total = gx * gy * gridDim.z;
+    if (b >= total) return;
+    const int bx = (int)(b % gx), by = (int)((b / gx) % gy), bz = (int)(b / (gx * gy));
+    const int x0 = bx * FTX;
+    constexpr int NU = 3 * FTZ * FTY, NS = (FTZ + 2) * FTY;
+    for (int t = tid; t < NU + 2 * NS; t += nt) {
+        if (t < NU) {
+            const int c = t / (FTZ * FTY), r = t % (FTZ * FTY);
+            const int y = by * FTY + r % FTY, z = bz * FTZ + r / FTY;
+            if (y < g.ny && z < g.nz)
+                prefetch_l2(static_cast<const TF*>(a.u) + (long long)c * g.cs + offs(g, x0, y, z));
+        } else {
+            const int r = (t - NU) % NS;
+            const int y = by * FTY + r % FTY, z = clampi(bz * FTZ - 1 + r / FTY, 0, g.nz - 1);
+            const TI* img = static_cast<const TI*>(t - NU < NS ? a.S : a.M);
+            if (y < g.ny) prefetch_l2(img + offs(g, x0, y, z));
+        }
+    }
+}
+
 template <int V>
 struct VT {
     static constexpr bool GM = (V == 2 || V == 3 || V == 4 || V == 5);  // warped gradient
@@ -120,6 +151,11 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
     const int x = bx0 + tx, y = by0 + ty;
     const bool col_valid = (x < g.nx) && (y < g.ny);
+    if (a.pf_stride > 0)
+        prefetch_brick<FTZ, TI, TF>(
+            a, blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z) +
+                   a.pf_stride,
+            tid, FNT);
     const int xc = min(x, g.nx - 1), yc = min(y, g.ny - 1);
     const int xm = max(xc - 1, 0), xp = min(xc + 1, g.nx - 1);
     const int ym = max(yc - 1, 0), yp = min(yc + 1, g.ny - 1);

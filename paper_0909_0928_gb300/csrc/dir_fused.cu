@@ -18,8 +18,10 @@
 #include <cuda_runtime.h>
 
 #include "dir_common.cuh"
+#include "dir_force_kernel.cuh"
 #include "dir_force_law.cuh"
 #include "dir_launch.h"
+#include "dir_smooth2.cuh"
 #include "dir_stencil.cuh"
 
 namespace dirk {
@@ -191,11 +193,265 @@ static cudaError_t launch_t(int variant, const FusedArgs& a, int num_sms, cudaSt
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Single-precision fused iteration on the packed smoothing of dir_smooth2.cuh.
+// A block of 384 threads owns a 32 x 16 column tile and a z chunk: three
+// groups of 128 threads smooth the three components of v_{k-1} plane by plane
+// (one TMA copy brings the plane box of all three), the smoothed plane u_k
+// goes through shared memory, and 256 threads then do the force work for its
+// 512 voxels, two each (rows r and r + 8).  S arrives by TMA too, one plane
+// box (tile + 1-voxel halo) per step into a ring that holds the planes zo - 1,
+// zo, zo + 1 of the output plane zo, so the static gradient and the reference
+// S(x) of the warped difference come from shared memory; M is gathered
+// through L1/L2.  The arithmetic of every voxel is that of the smoothing and
+// force kernels (same building blocks, same order).
+// ---------------------------------------------------------------------------
+constexpr int F2T = 3 * S2T;            // 384 threads
+constexpr int F2ST = 4;                 // stages of the v plane ring
+constexpr int F2SST = F2ST + 3;         // S ring: 3 planes read, F2ST - 1 in flight, 1 spare
+constexpr int F2SX = 4;                 // S box x halo (16-byte aligned start)
+constexpr int F2SW = S2X + 2 * F2SX;    // S box width: x0 - 4 .. x0 + 35
+constexpr int F2SH = S2Y + 2;           // S box rows: y0 - 1 .. y0 + 16
+
+template <int R>
+struct F2Geom {
+    using G = S2Geom<R>;
+    static constexpr int VBOX = 3 * G::SLOT;  // the plane box of all three components
+    static constexpr int VSTRIDE = (VBOX + 127) / 128 * 128;
+    static constexpr int SBOX = F2SH * F2SW * 4;
+    static constexpr int SSTRIDE = (SBOX + 127) / 128 * 128;
+    static constexpr int UTILE = 3 * S2Y * S2X * 4;
+    static constexpr int OFF_S = F2ST * VSTRIDE;
+    static constexpr int OFF_TXP = OFF_S + F2SST * SSTRIDE;
+    static constexpr int OFF_U = OFF_TXP + 3 * G::TXP_STRIDE;
+    static constexpr int OFF_BAR = OFF_U + UTILE;
+    static constexpr int SMEM = 128 + OFF_BAR + 64;
+};
+
+template <int R, int V>
+__global__ void __launch_bounds__(F2T, 2)
+    fused2_kernel(const __grid_constant__ CUtensorMap vmap, const __grid_constant__ CUtensorMap smap,
+                  const FusedArgs a, int zchunk) {
+    static_assert(V == 0 || V == 1, "fused iteration needs no warped-image gradient");
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    using G = S2Geom<R>;
+    using F = F2Geom<R>;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + F::OFF_BAR);
+    float* utile = reinterpret_cast<float*>(base + F::OFF_U);  // [3][S2Y][S2X]
+    const Grid3 g = a.g;
+    const float* __restrict__ M = static_cast<const float*>(a.M);
+    float* __restrict__ vout = static_cast<float*>(a.v);
+    float w[R + 1];
+    f32x2 wp[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+        w[t] = a.taps.wf[t];
+        wp[t] = f2_pack(w[t], w[t]);
+    }
+    const int tid = threadIdx.x;
+    const int grp = tid >> 7, gt = tid & 127;  // smoothing: component group, thread in it
+    const int lx = gt & 31, q = gt >> 5;
+    f32x2* txp = reinterpret_cast<f32x2*>(base + F::OFF_TXP + grp * G::TXP_STRIDE);
+    float* txf = reinterpret_cast<float*>(txp);
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * S2Y;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const int nsteps = (z1 - z0) + 2 * R;
+    const int bx = x0 - HA, by = y0 - R;
+    const int sbx = x0 - F2SX, sby = y0 - 1;
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
+
+    // step s loads the v planes z0 - R + s and the S plane z0 - 2R + 1 + s
+    // (the plane above the output plane of that step), both clamped
+    auto issue = [&](int step) {
+        const int sl = step % F2ST;
+        const int pv = clampi(z0 - R + step, 0, g.nz - 1);
+        const int ps = clampi(z0 - 2 * R + 1 + step, 0, g.nz - 1);
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[sl], (uint32_t)(F::VBOX + F::SBOX));
+        tma_load_4d(base + sl * F::VSTRIDE, &vmap, bx, by, pv, 0, &full[sl]);
+        tma_load_4d(base + F::OFF_S + (step % F2SST) * F::SSTRIDE, &smap, sbx, sby, ps, 0,
+                    &full[sl]);
+    };
+    if (tid == 0) {
+        for (int sl = 0; sl < F2ST; ++sl) mbar_init(&full[sl], 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        for (int st = 0; st < F2ST - 1 && st < nsteps; ++st) issue(st);
+    }
+    __syncthreads();
+
+    f32x2 ring[K][2];
+#pragma unroll
+    for (int t = 0; t < K; ++t) ring[t][0] = ring[t][1] = 0ull;
+
+    // force role: threads 0..255, column fx, rows fr and fr + 8 of the tile
+    const bool forcer = tid < 2 * S2T;
+    const int fx = tid & 31, fr = (tid >> 5) & 7;
+    const int x = x0 + fx;
+    const int xc = min(x, g.nx - 1);
+    const int sxm = max(xc - 1, 0) - sbx, sxc = xc - sbx, sxp = min(xc + 1, g.nx - 1) - sbx;
+    const Interp ip(g);
+    const int cs = (int)g.cs;
+    float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+
+    for (int step = 0; step < nsteps; ++step) {
+        if (tid == 0 && step + F2ST - 1 < nsteps) issue(step + F2ST - 1);
+        const int sl = step % F2ST;
+        const uint32_t parity = (uint32_t)((step / F2ST) & 1);
+        bool ok = true;
+        if (tid == 0) ok = mbar_wait_bounded(&full[sl], parity, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+            return;
+        }
+        (void)mbar_try_wait(&full[sl], parity);
+        float* vslots = reinterpret_cast<float*>(base + sl * F::VSTRIDE);  // [3][H][WB]
+        if (edge) s2_edge_fix<R>(vslots, H * WB, 3, bx, by, g, tid, F2T);
+        s2_xpass<R>(vslots + grp * H * WB, txf, gt, w);
+        __syncthreads();
+        const bool emit = step >= 2 * R;
+        S2_RING_SWITCH(R, step % K, {
+            s2_y<R, J>(txp, q, lx, wp, ring);
+            if (emit) {
+                f32x2 r0, r1;
+                s2_z<R, J>(wp, ring, r0, r1);
+                float a0, b0, a1, b1;
+                f2_unpack(r0, a0, b0);
+                f2_unpack(r1, a1, b1);
+                float* ut = utile + grp * (S2Y * S2X) + lx;
+                ut[(2 * q) * S2X] = a0;
+                ut[(2 * q + 1) * S2X] = a1;
+                ut[(2 * q + S2Y / 2) * S2X] = b0;
+                ut[(2 * q + S2Y / 2 + 1) * S2X] = b1;
+            }
+        })
+        if (!emit) continue;  // uniform
+        __syncthreads();
+        if (forcer) {
+            const int zo = z0 + step - 2 * R;
+            // S planes zo - 1, zo, zo + 1 (clamped) from the ring
+            const float* Sm = reinterpret_cast<const float*>(
+                base + F::OFF_S + ((step + F2SST - 2) % F2SST) * F::SSTRIDE);
+            const float* Sc = reinterpret_cast<const float*>(
+                base + F::OFF_S + ((step + F2SST - 1) % F2SST) * F::SSTRIDE);
+            const float* Sp =
+                reinterpret_cast<const float*>(base + F::OFF_S + (step % F2SST) * F::SSTRIDE);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = fr + h * (S2Y / 2);
+                const int y = y0 + row;
+                if (x < g.nx && y < g.ny) {
+                    const int syc = y - sby, sym = max(y - 1, 0) - sby, syp = min(y + 1, g.ny - 1) - sby;
+                    const float ux = utile[(0 * S2Y + row) * S2X + fx];
+                    const float uy = utile[(1 * S2Y + row) * S2X + fx];
+                    const float uz = utile[(2 * S2Y + row) * S2X + fx];
+                    const float s0 = Sc[syc * F2SW + sxc];
+                    const float gsx = 0.5f * (Sc[syc * F2SW + sxp] - Sc[syc * F2SW + sxm]);
+                    const float gsy = 0.5f * (Sc[syp * F2SW + sxc] - Sc[sym * F2SW + sxc]);
+                    const float gsz = 0.5f * (Sp[syc * F2SW + sxc] - Sm[syc * F2SW + sxc]);
+                    const float d = interp_rel(M, ip, x, ux, y, uy, zo, uz, s0);  // W - S
+                    float bm = 0.0f;
+                    if (V == 1) {
+                        const int o = offs(g, x, y, zo);
+                        const int xm = max(x - 1, 0), xp = min(x + 1, g.nx - 1);
+                        const int ro = o - x;
+                        const float mx = 0.5f * (__ldg(M + ro + xp) - __ldg(M + ro + xm));
+                        const float my = 0.5f * (__ldg(M + offs(g, x, min(y + 1, g.ny - 1), zo)) -
+                                                 __ldg(M + offs(g, x, max(y - 1, 0), zo)));
+                        const float mz = 0.5f * (__ldg(M + offs(g, x, y, min(zo + 1, g.nz - 1))) -
+                                                 __ldg(M + offs(g, x, y, max(zo - 1, 0))));
+                        bm = r_sqrt(mx * mx + my * my + mz * mz);
+                    }
+                    float dx, dy, dz;
+                    demons_force<float, V>(d, gsx, gsy, gsz, 0.0f, 0.0f, 0.0f, bm, 0.0f, dx, dy, dz);
+                    dx = -dx;
+                    dy = -dy;
+                    dz = -dz;
+                    sd2 += d * d;
+                    sdu += r_norm_fast(dx * dx + dy * dy + dz * dz);
+                    su += r_norm_fast(ux * ux + uy * uy + uz * uz);
+                    const int o = offs(g, x, y, zo);
+                    vout[o] = ux + dx;
+                    vout[o + cs] = uy + dy;
+                    vout[o + 2 * cs] = uz + dz;
+                }
+            }
+        }
+        // the next step's __syncthreads_or orders these reads of the u tile and
+        // of the S ring before they are rewritten
+    }
+    block_reduce3_atomic<F2T, float>(sd2, sdu, su, a.red);
+}
+
+template <int R>
+static bool make_f2_maps(CUtensorMap* vmap, CUtensorMap* smap, const FusedArgs& a) {
+    using G = S2Geom<R>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const Grid3& g = a.g;
+    const cuuint64_t vdims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t sdims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 1};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                   (cuuint64_t)g.cs * 4};
+    const cuuint32_t vbox[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, 1u, 3u};
+    const cuuint32_t sbox[4] = {(cuuint32_t)F2SW, (cuuint32_t)F2SH, 1u, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    auto ok = [&](CUtensorMap* m, const void* p, const cuuint64_t* d, const cuuint32_t* b) {
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(p), d, strides, b, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
+    };
+    return ok(vmap, a.vin, vdims, vbox) && ok(smap, a.S, sdims, sbox);
+}
+
+template <int R, int V>
+static cudaError_t launch_f2(const FusedArgs& a, int num_sms, cudaStream_t s) {
+    using F = F2Geom<R>;
+    CUtensorMap vmap, smap;
+    if (!make_f2_maps<R>(&vmap, &smap, a)) return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    static int per_sm = 1;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<R, V>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused2_kernel<R, V>, F2T, F::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles = ((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + S2Y - 1) / S2Y);
+    long long chunks = ((long long)(per_sm < 1 ? 1 : per_sm) * num_sms) / tiles;
+    if (chunks < 1) chunks = 1;
+    if (chunks > a.g.nz) chunks = a.g.nz;
+    const int zc = (int)((a.g.nz + chunks - 1) / chunks);
+    const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + S2Y - 1) / S2Y, (a.g.nz + zc - 1) / zc);
+    fused2_kernel<R, V><<<grid, dim3(F2T, 1, 1), F::SMEM, s>>>(vmap, smap, a, zc);
+    return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_f2r(int variant, const FusedArgs& a, int num_sms, cudaStream_t s) {
+    return variant == 1 ? launch_f2<R, 1>(a, num_sms, s) : launch_f2<R, 0>(a, num_sms, s);
+}
+
 bool fused_supported(int variant) { return variant == 0 || variant == 1; }
 
 cudaError_t launch_fused(int variant, bool fp64, const FusedArgs& a, int num_sms, cudaStream_t s) {
     if (!fused_supported(variant)) return cudaErrorInvalidValue;
-    return fp64 ? launch_t<double>(variant, a, num_sms, s) : launch_t<float>(variant, a, num_sms, s);
+    if (fp64) return launch_t<double>(variant, a, num_sms, s);
+    switch (a.taps.R) {  // the packed kernel for the usual radii
+        case 1: return launch_f2r<1>(variant, a, num_sms, s);
+        case 2: return launch_f2r<2>(variant, a, num_sms, s);
+        case 3: return launch_f2r<3>(variant, a, num_sms, s);
+        case 4: return launch_f2r<4>(variant, a, num_sms, s);
+        default: return launch_t<float>(variant, a, num_sms, s);
+    }
 }
 
 }  // namespace dirk

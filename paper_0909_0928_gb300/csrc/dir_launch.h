@@ -29,6 +29,8 @@ struct ForceArgs {
     int depth;           // voxels per thread along z: 1, 2, 4 or 8
     int img_type;        // storage of S and M at this level (kStore*)
     int field_type;      // storage of u and v (kStore*)
+    int pf_stride = 0;   // > 0: each block prefetches into L2 the brick of the block
+                         // this many linear indices ahead (about one wave)
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
 int force_brick_depth(const Grid3& g, int num_sms, int waves);

@@ -12,6 +12,7 @@
 
 #include "dir_common.cuh"
 #include "dir_launch.h"
+#include "dir_smooth2.cuh"
 #include "dir_stencil.cuh"
 
 namespace dirk {
@@ -68,129 +69,33 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8, TIN>::YT)
 
 
 // ---------------------------------------------------------------------------
-// Single-precision field smoothing, packed.  A block of 128 threads smooths
-// one component of a 32 x 16 (x, y) tile over a z chunk.  Each input plane
-// (tile + halo, H = 16 + 2R rows) arrives by TMA into a 4-slot ring; the x
-// pass (scalar, 4 outputs per task from 128-bit shared loads) writes its rows
-// into a pair-interleaved buffer in which row m sits beside row m + 8, so that
-// the y and z passes run on f32x2 pairs (rows y and y + 8 of one column): a
-// thread owns column lx and rows {2q, 2q+1, 2q+8, 2q+9}, filters them in y
-// from 64-bit shared loads, keeps the 2R+1 most recent y-filtered planes in
-// registers and filters them in z.  The y and z passes are instantiated for
-// each ring position (a switch on the plane index modulo 2R+1), so the
-// register ring rotates by renaming, not by moves, without unrolling the
-// whole plane loop.
+// Single-precision field smoothing, packed (building blocks and layout in
+// dir_smooth2.cuh): a block of 128 threads smooths one component of a
+// 32 x 16 tile over a z chunk, fed by a 6-deep ring of TMA plane copies.
 // ---------------------------------------------------------------------------
-constexpr int S2X = 32, S2Y = 16, S2T = 128, S2STAGES = 6;
-constexpr int S2TP = S2X + 1;  // pair-row pitch in f32x2 (the pad staggers banks)
+constexpr int S2STAGES = 6;
 
 template <int R>
-struct S2Geom {
-    static constexpr int K = 2 * R + 1;
-    static constexpr int H = S2Y + 2 * R;                // box rows
-    static constexpr int HA = (R + 3) / 4 * 4;           // x halo: TMA x start 16-byte aligned
-    static constexpr int WB = S2X + 2 * HA;              // box width
-    static constexpr int NPR = S2Y / 2 + 2 * R;          // pair rows (m, m + 8)
-    static constexpr int XLV = (HA - R + 4 + 2 * R + 3) / 4 * 4;  // x-task inputs, whole float4s
-    static constexpr int SLOT = H * WB * 4;              // bytes per stage
-    static constexpr int SLOT_STRIDE = (SLOT + 127) / 128 * 128;
-    static constexpr int TXP = NPR * S2TP * 8;
-    static constexpr int SMEM = 128 + S2STAGES * SLOT_STRIDE + (TXP + 127) / 128 * 128 + 64;
-};
-
-
-// y pass of one plane into ring slot J, then (once 2R+1 planes are in) the z
-// pass over the ring, oldest plane first, and the stores of output plane zo
-template <int R, int J>
-__device__ __forceinline__ void s2_yz(const f32x2* __restrict__ txp, int q, int lx,
-                                      const f32x2 (&wp)[R + 1], f32x2 (&ring)[2 * R + 1][2],
-                                      bool emit, float* __restrict__ o, int px, int rows_left) {
-    constexpr int K = 2 * R + 1;  // taps are symmetric: tap t is wp[min(t, 2R - t)]
-    f32x2 in2[K + 1];
-#pragma unroll
-    for (int m = 0; m < K + 1; ++m) in2[m] = txp[(2 * q + m) * S2TP + lx];
-    f32x2 p0 = 0ull, p1 = 0ull;
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        p0 = f2_fma(wp[t <= R ? t : 2 * R - t], in2[t], p0);
-        p1 = f2_fma(wp[t <= R ? t : 2 * R - t], in2[t + 1], p1);
-    }
-    ring[J][0] = p0;
-    ring[J][1] = p1;
-    if (emit) {
-        f32x2 r0 = 0ull, r1 = 0ull;
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            r0 = f2_fma(wp[t <= R ? t : 2 * R - t], ring[(J + 1 + t) % K][0], r0);
-            r1 = f2_fma(wp[t <= R ? t : 2 * R - t], ring[(J + 1 + t) % K][1], r1);
-        }
-        float a0, b0, a1, b1;
-        f2_unpack(r0, a0, b0);
-        f2_unpack(r1, a1, b1);
-        // rows ya, ya + 1, ya + 8, ya + 9; rows_left = ny - ya (x checked by the caller)
-        if (rows_left > 0) o[0] = a0;
-        if (rows_left > 1) o[px] = a1;
-        if (rows_left > S2Y / 2) o[(S2Y / 2) * px] = b0;
-        if (rows_left > S2Y / 2 + 1) o[(S2Y / 2 + 1) * px] = b1;
-    }
-}
-
-
-// x pass of one task: box row rho, outputs 4 gq .. 4 gq + 3, written to the
-// pair rows (rho as the upper lane of pair row rho, the lower lane of pair
-// row rho - 8)
-template <int R>
-__device__ __forceinline__ void s2_xtask(const float* __restrict__ slot, float* __restrict__ txf,
-                                         int tk, const float (&w)[R + 1]) {
+struct S2Smem {
     using G = S2Geom<R>;
-    constexpr int K = 2 * R + 1, HA = G::HA, WB = G::WB, NPR = G::NPR;
-    const int gq = tk & 7, rho = tk >> 3;
-    const float* src = slot + rho * WB + 4 * gq;
-    float in[G::XLV];
-#pragma unroll
-    for (int v = 0; v < G::XLV / 4; ++v) {
-        const float4 t4 = reinterpret_cast<const float4*>(src)[v];
-        in[4 * v] = t4.x;
-        in[4 * v + 1] = t4.y;
-        in[4 * v + 2] = t4.z;
-        in[4 * v + 3] = t4.w;
-    }
-    float o[4];
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < K; ++t) acc = fmaf(w[t <= R ? t : 2 * R - t], in[HA - R + jj + t], acc);
-        o[jj] = acc;
-    }
-    if (rho < NPR) {
-        float* d = txf + 2 * (rho * S2TP + 4 * gq);
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
-    }
-    if (rho >= S2Y / 2) {
-        float* d = txf + 2 * ((rho - S2Y / 2) * S2TP + 4 * gq) + 1;
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
-    }
-}
+    static constexpr int SMEM = 128 + S2STAGES * G::SLOT_STRIDE + G::TXP_STRIDE + 64;
+};
 
 template <int R>
 __global__ void __launch_bounds__(S2T, 8)
     smooth2_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
     using G = S2Geom<R>;
-    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB, NPR = G::NPR;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB;
     extern __shared__ unsigned char smem_raw[];
-    // 128-byte aligned, by pointer arithmetic on the shared array (keeps the
+    // 128-byte aligned by pointer arithmetic on the shared array (keeps the
     // accesses below in the shared address space)
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     f32x2* txp = reinterpret_cast<f32x2*>(base + S2STAGES * G::SLOT_STRIDE);
     float* txf = reinterpret_cast<float*>(txp);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + S2STAGES * G::SLOT_STRIDE +
-                                                 (G::TXP + 127) / 128 * 128);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + S2STAGES * G::SLOT_STRIDE + G::TXP_STRIDE);
     const Grid3 g = a.g;
-    float w[R + 1];  // symmetric taps: w[t] for t = 0..R (outermost first)
+    float w[R + 1];  // symmetric taps w[0..R]
     f32x2 wp[R + 1];
 #pragma unroll
     for (int t = 0; t <= R; ++t) {
@@ -243,40 +148,25 @@ __global__ void __launch_bounds__(S2T, 8)
         }
         (void)mbar_try_wait(&full[sl], parity);
         float* slot = reinterpret_cast<float*>(base + sl * G::SLOT_STRIDE);  // [H][WB]
-        if (edge) {  // replicate boundary: columns per row, then rows per column
-            const int lo = max(0, -bx), hi = min(WB, g.nx - bx);
-            for (int row = tid; row < H; row += S2T) {
-                float* r = slot + row * WB;
-                const float left = r[lo], right = r[hi - 1];
-                for (int hx = 0; hx < lo; ++hx) r[hx] = left;
-                for (int hx = hi; hx < WB; ++hx) r[hx] = right;
-            }
-            __syncthreads();
-            const int rlo = max(0, -by), rhi = min(H, g.ny - by);
-            for (int col = tid; col < WB; col += S2T) {
-                float* c = slot + col;
-                const float top = c[rlo * WB], bot = c[(rhi - 1) * WB];
-                for (int hy = 0; hy < rlo; ++hy) c[hy * WB] = top;
-                for (int hy = rhi; hy < H; ++hy) c[hy * WB] = bot;
-            }
-            __syncthreads();
-        }
-        // x pass: H * 8 tasks (between 128 and 256 for R = 1..4)
-        static_assert(H * (S2X / 4) > S2T && H * (S2X / 4) <= 2 * S2T, "x tasks per thread");
-        s2_xtask<R>(slot, txf, tid, w);
-        if (tid < H * (S2X / 4) - S2T) s2_xtask<R>(slot, txf, tid + S2T, w);
+        if (edge) s2_edge_fix<R>(slot, G::SLOT_STRIDE / 4, 1, bx, by, g, tid, S2T);
+        s2_xpass<R>(slot, txf, tid, w);
         __syncthreads();
         const bool emit = step >= 2 * R;
         float* o = out + offs(g, x < g.nx ? x : 0, ya, emit ? z0 + step - 2 * R : 0);
-        switch (step % K) {
-#define S2_CASE(J)                                                          \
-    case J:                                                                 \
-        if constexpr (J < K) s2_yz<R, J>(txp, q, lx, wp, ring, emit, o, px, rows_left); \
-        break;
-            S2_CASE(0) S2_CASE(1) S2_CASE(2) S2_CASE(3) S2_CASE(4) S2_CASE(5) S2_CASE(6)
-            S2_CASE(7) S2_CASE(8)
-#undef S2_CASE
-        }
+        S2_RING_SWITCH(R, step % K, {
+            s2_y<R, J>(txp, q, lx, wp, ring);
+            if (emit) {
+                f32x2 r0, r1;
+                s2_z<R, J>(wp, ring, r0, r1);
+                float a0, b0, a1, b1;
+                f2_unpack(r0, a0, b0);
+                f2_unpack(r1, a1, b1);
+                if (rows_left > 0) o[0] = a0;
+                if (rows_left > 1) o[px] = a1;
+                if (rows_left > S2Y / 2) o[(S2Y / 2) * px] = b0;
+                if (rows_left > S2Y / 2 + 1) o[(S2Y / 2 + 1) * px] = b1;
+            }
+        })
         // no barrier here: the next step's __syncthreads_or orders this
         // step's reads of the pair rows before the next x pass rewrites them
     }
@@ -312,7 +202,7 @@ static int s2_zchunk(const Grid3& g, int per_sm, int num_sms, int ncomp) {
 
 template <int R>
 static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    using G = S2Geom<R>;
+    using G = S2Smem<R>;
     CUtensorMap map;
     if (!make_s2_map<R>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation

@@ -354,6 +354,24 @@ def test_fused_schedule_matches_two_kernel_schedule(dl, small_phantom, variant, 
     np.testing.assert_allclose(a["hist"], b["hist"], rtol=1e-5 if not fp64 else 1e-12)
 
 
+@pytest.mark.parametrize("dims", [(45, 37, 19), (70, 9, 33), (100, 60, 41)])
+def test_fused_schedule_ragged(dl, dims):
+    # partial tiles in x and y, odd z chunks, three levels: the fused kernel
+    # against the two-kernel schedule and the oracle
+    import oracle
+    from phantom import PhantomSpec, make_lung_phantom
+    spec = PhantomSpec(dims=dims, spacing=(1.2, 1.2, 2.5), seed=31, a_max_mm=5.0,
+                       compression=0.1, n_vessels=12, n_landmarks=50)
+    p = make_lung_phantom(spec)
+    S, M = p["S"], p["M"]
+    a = gpu_register(dl, S, M, 0, 3, [12, 8, 6], fuse=1)
+    b = gpu_register(dl, S, M, 0, 3, [12, 8, 6], fuse=0)
+    diff = float(np.abs(a["u"] - b["u"]).max())
+    assert diff <= 1e-5, diff
+    ref = oracle.register(S, M, variant=0, levels=3, iters=[12, 8, 6])
+    check32(oracle, S, M, a, ref, probe(S, M, 0, 3, [12, 8, 6], ref, F32_NOISE), f"{dims} fused")
+
+
 # ------------------------------------------------------------- full size
 
 FULL_VARIANTS = [(0, 0.4), (1, 0.4), (2, 0.4), (3, 0.4), (4, 0.4), (4, 2.0), (5, 0.4)]
@@ -377,6 +395,10 @@ def test_full_size_parity(dl, full_phantom, variant, alpha):
                                spread32))
     g = gpu_register(dl, S, M, variant, spacing=(0.9, 0.9, 2.5), **sched)
     check32(oracle, S, M, g, ref, spread32, f"full v{variant} a{alpha}")
+    if variant in (0, 1):
+        # the default schedule: fused iterations on the two coarse levels
+        gf = gpu_register(dl, S, M, variant, spacing=(0.9, 0.9, 2.5), fuse=2, **sched)
+        check32(oracle, S, M, gf, ref, spread32, f"full v{variant} fused coarse levels")
     # synthetic landmark accuracy (Sec. 3.2 evaluation): error well below motion
     lm, sp = full_phantom["landmarks"], full_phantom["spacing"]
     ue = np.stack([oracle.interp(g["u"][c].astype(np.float64), lm[:, 0], lm[:, 1], lm[:, 2])
