@@ -175,18 +175,29 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def cpu_baseline(phantom, variant, alpha, iters_sample):
-    """The FP64 oracle as it stands, threaded over z-slices on the host cores."""
+def cpu_baseline(phantom, variant, alpha, iters_sample, single_thread_sample=None):
+    """The FP64 oracle as it stands, threaded over z-slices on the host cores
+    (and, if asked, single-threaded on a smaller sample)."""
     import oracle
     t0 = time.perf_counter()
     r = oracle.register(phantom["S"], phantom["M"], variant=variant, levels=LEVELS,
                         iters=iters_sample, alpha=alpha, threaded=True)
     dt = time.perf_counter() - t0
     vu = voxel_updates(DIMS, LEVELS, iters_sample)
-    return {"value": vu / dt, "unit": UNIT, "cores": oracle.num_threads(True), "kind": "oracle",
-            "sample": f"full-size phantom, {LEVELS} levels at {'/'.join(map(str, iters_sample))} "
-                      f"iterations coarse to fine ({vu} voxel-updates, {dt:.1f} s)",
-            "seconds": dt, "iters_run": r["iters_run"]}
+    out = {"value": vu / dt, "unit": UNIT, "cores": oracle.num_threads(True), "kind": "oracle",
+           "sample": f"full-size phantom, {LEVELS} levels at {'/'.join(map(str, iters_sample))} "
+                     f"iterations coarse to fine ({vu} voxel-updates, {dt:.1f} s)",
+           "seconds": dt, "iters_run": r["iters_run"]}
+    if single_thread_sample:
+        t0 = time.perf_counter()
+        oracle.register(phantom["S"], phantom["M"], variant=variant, levels=LEVELS,
+                        iters=single_thread_sample, alpha=alpha, threaded=False)
+        d1 = time.perf_counter() - t0
+        v1 = voxel_updates(DIMS, LEVELS, single_thread_sample)
+        out["single_thread"] = {"value": v1 / d1, "unit": UNIT, "cores": 1,
+                                "sample": f"{'/'.join(map(str, single_thread_sample))} iterations "
+                                          f"({v1} voxel-updates, {d1:.1f} s)"}
+    return out
 
 
 def run_reference(args):
@@ -392,8 +403,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--form", default="plain", choices=["plain", "batch", "study"])
-    ap.add_argument("--fuse", type=int, default=0, choices=[0, 1],
-                    help="fold the Gaussian into the next force pass (Eqs. 1-2)")
+    ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2],
+                    help="fold the Gaussian into the next force pass (Eqs. 1-2): 0 never, "
+                         "1 every level, 2 (library default) levels up to 2M voxels")
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
@@ -537,8 +549,8 @@ def main():
     dl.dir_destroy(ctx)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(ph, args.variant_id, args.alpha, [40, 20, 10])
-        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cb = cpu_baseline(ph, args.variant_id, args.alpha, [40, 20, 10], [8, 4, 2])
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "single_thread")}
 
     if rank == 0:
         srt = sorted(step_ms)

@@ -14,7 +14,8 @@ module only schedules.
 
     python -m paper_0909_0928_gb300.serve --rates 1 2 5 10 20 --jobs 40
 
-prints one JSON line per arrival rate with p50/p99 latency and volumes/s.
+prints one JSON line per arrival rate with p50/p99 latency and volumes/s, for
+the same request stream served one job at a time and with continuous batching.
 """
 from __future__ import annotations
 
@@ -199,7 +200,7 @@ DEFAULT_SIZES = [(128, 128, 64), (192, 192, 96), (256, 256, 128), (384, 384, 128
 
 
 def make_requests(n: int, rate: float, seed: int, sizes=DEFAULT_SIZES,
-                  a_max_mm: float = 15.0, iters=(200, 100, 50)) -> list[Request]:
+                  a_max_mm: float = 15.0, iters=(200, 100, 50), use_graph: int = 0) -> list[Request]:
     """Poisson arrivals at `rate` jobs/s; each request takes one of the pooled
     phantoms (sizes spanning 128x128x64 .. 512x512x160, up to a_max_mm of RBF
     motion) and a force law uniform over the six, 3-level pyramid."""
@@ -212,7 +213,9 @@ def make_requests(n: int, rate: float, seed: int, sizes=DEFAULT_SIZES,
         t += -math.log(1.0 - float(rng.uniform(1)[0])) / rate
         S, M, spacing = pool[int(float(rng.uniform(1)[0]) * len(pool)) % len(pool)]
         variant = int(float(rng.uniform(1)[0]) * 6) % 6
-        params = dir_params_default(levels=3, iters=list(iters))
+        # one registration per context: launching directly costs less host time
+        # than capturing a graph that would be replayed only once
+        params = dir_params_default(levels=3, iters=list(iters), use_graph=use_graph)
         out.append(Request(rid=k, S=S, M=M, spacing=spacing, variant=variant, params=params,
                            arrival=t))
     return out
@@ -224,14 +227,20 @@ def main():
     ap.add_argument("--jobs", type=int, default=30)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--graph", type=int, default=0, help="capture each job's registration")
     args = ap.parse_args()
     import torch
     torch.cuda.init()
+    warm = make_requests(4, 100.0, args.seed + 1, use_graph=args.graph)  # first contexts
+    Server(slots=2, keep_fields=False).run(warm, realtime=False)
     for rate in args.rates:
-        reqs = make_requests(args.jobs, rate, args.seed)
-        srv = Server(slots=args.slots, keep_fields=False)
-        done = srv.run(reqs, realtime=True)
-        line = {"mode": "serve", "rate_jobs_per_s": rate, "slots": args.slots, **latency_stats(done)}
+        line = {"mode": "serve", "rate_jobs_per_s": rate, "jobs": args.jobs}
+        # the same Poisson stream, served one job at a time (a plain queue of
+        # per-pair registrations) and with continuous batching over the slots
+        for name, slots in (("plain_queue", 1), ("continuous_batching", args.slots)):
+            reqs = make_requests(args.jobs, rate, args.seed, use_graph=args.graph)
+            done = Server(slots=slots, keep_fields=False).run(reqs, realtime=True)
+            line[name] = {"slots": slots, **latency_stats(done)}
         print(json.dumps(line), flush=True)
 
 
