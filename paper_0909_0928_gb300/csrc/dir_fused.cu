@@ -435,8 +435,236 @@ static cudaError_t launch_f2(const FusedArgs& a, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused iteration for small levels (where the marching kernel would get z
+// chunks of one or two planes and spend each iteration waiting on a chain of
+// plane steps): a block of 384 threads owns a 32 x 16 tile and FZC = 2 output
+// planes, fetches the FZC + 2R input planes of all three components in ONE
+// TMA copy (plus the S planes zo - 1 .. zo + FZC), and runs every pass over all
+// planes at once: x pass of all planes, y pass into per-plane pair rows, z pass
+// with the clamped plane indices, then the force work.  One copy latency and
+// four barriers per iteration instead of 2R + FZC sequential steps.  Same
+// building blocks and order of operations as the marching kernels.
+// ---------------------------------------------------------------------------
+constexpr int FZC = 2;
+
+template <int R>
+struct FSGeom {
+    using G = S2Geom<R>;
+    static constexpr int NP = FZC + 2 * R;                          // input planes
+    static constexpr int PLANE = G::H * G::WB;                      // floats per plane box
+    static constexpr int VBOX = 3 * NP * PLANE * 4;                 // [3][NP][H][WB]
+    static constexpr int SNP = FZC + 2;                             // S planes
+    static constexpr int SBOX = SNP * F2SH * F2SW * 4;              // [SNP][F2SH][F2SW]
+    static constexpr int YPL = (S2Y / 2) * S2X;                     // f32x2 per y-filtered plane
+    static constexpr int OFF_S = (VBOX + 127) / 128 * 128;
+    static constexpr int OFF_TXP = OFF_S + (SBOX + 127) / 128 * 128;
+    static constexpr int OFF_U = OFF_TXP + 3 * NP * G::TXP_STRIDE;
+    static constexpr int UT = FZC * 3 * S2Y * S2X * 4;              // [FZC][3][S2Y][S2X]
+    static constexpr int OFF_BAR = OFF_U + UT;
+    static constexpr int SMEM = 128 + OFF_BAR + 64;
+    static_assert(3 * NP * YPL * 8 <= VBOX, "y-filtered planes reuse the plane boxes");
+};
+
+template <int R, int V>
+__global__ void __launch_bounds__(F2T, 1)
+    fused_small_kernel(const __grid_constant__ CUtensorMap vmap,
+                       const __grid_constant__ CUtensorMap smap, const FusedArgs a) {
+    static_assert(V == 0 || V == 1, "fused iteration needs no warped-image gradient");
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    using G = S2Geom<R>;
+    using F = FSGeom<R>;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB, NP = F::NP;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + F::OFF_BAR);
+    float* vbox = reinterpret_cast<float*>(base);                      // [3][NP][H][WB]
+    f32x2* ypl = reinterpret_cast<f32x2*>(base);                       // [3][NP][8][32], after x
+    const float* sbox = reinterpret_cast<const float*>(base + F::OFF_S);  // [SNP][F2SH][F2SW]
+    float* utile = reinterpret_cast<float*>(base + F::OFF_U);          // [FZC][3][S2Y][S2X]
+    const Grid3 g = a.g;
+    const float* __restrict__ M = static_cast<const float*>(a.M);
+    float* __restrict__ vout = static_cast<float*>(a.v);
+    float w[R + 1];
+    f32x2 wp[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+        w[t] = a.taps.wf[t];
+        wp[t] = f2_pack(w[t], w[t]);
+    }
+    const int tid = threadIdx.x;
+    const int grp = tid >> 7, gt = tid & 127;
+    const int lx = gt & 31, q = gt >> 5;
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * S2Y;
+    const int z0 = blockIdx.z * FZC;
+    const int zb = z0 - R;       // z of box plane 0 (v)
+    const int zs = z0 - 1;       // z of box plane 0 (S)
+    const int bx = x0 - HA, by = y0 - R;
+    const int sbx = x0 - F2SX, sby = y0 - 1;
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
+    // input planes inside the volume (the others are zero-filled by the copy
+    // and never read: every plane index below is clamped into [pa, pb])
+    const int pa = max(0, -zb), pb = min(NP - 1, g.nz - 1 - zb);
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, (uint32_t)(F::VBOX + F::SBOX));
+        tma_load_4d(vbox, &vmap, bx, by, zb, 0, bar);
+        tma_load_4d(base + F::OFF_S, &smap, sbx, sby, zs, 0, bar);
+    }
+    __syncthreads();
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+        return;
+    }
+    (void)mbar_try_wait(bar, 0);
+    if (edge) s2_edge_fix<R>(vbox, H * WB, 3 * NP, bx, by, g, tid, F2T);
+    // x pass of every in-volume plane of this group's component
+    f32x2* txp_c = reinterpret_cast<f32x2*>(base + F::OFF_TXP) + (size_t)grp * NP * (G::TXP_STRIDE / 8);
+    for (int p = pa; p <= pb; ++p)
+        s2_xpass<R>(vbox + (grp * NP + p) * F::PLANE,
+                    reinterpret_cast<float*>(txp_c + p * (G::TXP_STRIDE / 8)), gt, w);
+    __syncthreads();
+    // y pass of every in-volume plane into the pair-row planes (the plane
+    // boxes are dead now); pairs (row 2q + j, row 2q + j + 8), j = 0, 1
+    for (int p = pa; p <= pb; ++p) {
+        const f32x2* tp = txp_c + p * (G::TXP_STRIDE / 8);
+        f32x2 in2[K + 1];
+#pragma unroll
+        for (int m = 0; m < K + 1; ++m) in2[m] = tp[(2 * q + m) * S2TP + lx];
+        f32x2 p0 = 0ull, p1 = 0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const f32x2 wt = wp[t <= R ? t : 2 * R - t];
+            p0 = f2_fma(wt, in2[t], p0);
+            p1 = f2_fma(wt, in2[t + 1], p1);
+        }
+        f32x2* yp = ypl + (size_t)(grp * NP + p) * F::YPL;
+        yp[(2 * q) * S2X + lx] = p0;
+        yp[(2 * q + 1) * S2X + lx] = p1;
+    }
+    __syncthreads();
+    // z pass of the output planes, oldest plane first, clamped plane indices
+#pragma unroll
+    for (int j = 0; j < FZC; ++j) {
+        if (z0 + j >= g.nz) break;
+        f32x2 r0 = 0ull, r1 = 0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const int pp = clampi(j + t, pa, pb);  // plane z0 + j - R + t, clamped
+            const f32x2* yp = ypl + (size_t)(grp * NP + pp) * F::YPL;
+            const f32x2 wt = wp[t <= R ? t : 2 * R - t];
+            r0 = f2_fma(wt, yp[(2 * q) * S2X + lx], r0);
+            r1 = f2_fma(wt, yp[(2 * q + 1) * S2X + lx], r1);
+        }
+        float a0, b0, a1, b1;
+        f2_unpack(r0, a0, b0);
+        f2_unpack(r1, a1, b1);
+        float* ut = utile + ((j * 3 + grp) * S2Y) * S2X + lx;
+        ut[(2 * q) * S2X] = a0;
+        ut[(2 * q + 1) * S2X] = a1;
+        ut[(2 * q + S2Y / 2) * S2X] = b0;
+        ut[(2 * q + S2Y / 2 + 1) * S2X] = b1;
+    }
+    __syncthreads();
+    // force work: FZC planes x 512 voxels over the 384 threads
+    const Interp ip(g);
+    const int cs = (int)g.cs;
+    const int spa = max(0, -zs), spb = min(F::SNP - 1, g.nz - 1 - zs);  // in-volume S planes
+    float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    for (int k = tid; k < FZC * S2Y * S2X; k += F2T) {
+        const int j = k / (S2Y * S2X), row = (k / S2X) % S2Y, fx = k % S2X;
+        const int x = x0 + fx, y = y0 + row, zo = z0 + j;
+        if (x >= g.nx || y >= g.ny || zo >= g.nz) continue;
+        const int sxc = x - sbx, sxm = max(x - 1, 0) - sbx, sxp = min(x + 1, g.nx - 1) - sbx;
+        const int syc = y - sby, sym = max(y - 1, 0) - sby, syp = min(y + 1, g.ny - 1) - sby;
+        const float* Sc = sbox + clampi(j + 1, spa, spb) * (F2SH * F2SW);
+        const float* Sm = sbox + clampi(j, spa, spb) * (F2SH * F2SW);
+        const float* Sp = sbox + clampi(j + 2, spa, spb) * (F2SH * F2SW);
+        const float* ut = utile + (j * 3 * S2Y + row) * S2X + fx;
+        const float ux = ut[0], uy = ut[S2Y * S2X], uz = ut[2 * S2Y * S2X];
+        const float s0 = Sc[syc * F2SW + sxc];
+        const float gsx = 0.5f * (Sc[syc * F2SW + sxp] - Sc[syc * F2SW + sxm]);
+        const float gsy = 0.5f * (Sc[syp * F2SW + sxc] - Sc[sym * F2SW + sxc]);
+        const float gsz = 0.5f * (Sp[syc * F2SW + sxc] - Sm[syc * F2SW + sxc]);
+        const float d = interp_rel(M, ip, x, ux, y, uy, zo, uz, s0);  // W - S
+        float bm = 0.0f;
+        if (V == 1) {
+            const int o = offs(g, x, y, zo);
+            const int ro = o - x;
+            const float mx = 0.5f * (__ldg(M + ro + min(x + 1, g.nx - 1)) - __ldg(M + ro + max(x - 1, 0)));
+            const float my = 0.5f * (__ldg(M + offs(g, x, min(y + 1, g.ny - 1), zo)) -
+                                     __ldg(M + offs(g, x, max(y - 1, 0), zo)));
+            const float mz = 0.5f * (__ldg(M + offs(g, x, y, min(zo + 1, g.nz - 1))) -
+                                     __ldg(M + offs(g, x, y, max(zo - 1, 0))));
+            bm = r_sqrt(mx * mx + my * my + mz * mz);
+        }
+        float dx, dy, dz;
+        demons_force<float, V>(d, gsx, gsy, gsz, 0.0f, 0.0f, 0.0f, bm, 0.0f, dx, dy, dz);
+        dx = -dx;
+        dy = -dy;
+        dz = -dz;
+        sd2 += d * d;
+        sdu += r_norm_fast(dx * dx + dy * dy + dz * dz);
+        su += r_norm_fast(ux * ux + uy * uy + uz * uz);
+        const int o = offs(g, x, y, zo);
+        vout[o] = ux + dx;
+        vout[o + cs] = uy + dy;
+        vout[o + 2 * cs] = uz + dz;
+    }
+    block_reduce3_atomic<F2T, float>(sd2, sdu, su, a.red);
+}
+
+// one block per SM with FZC-plane chunks covers the level
+static bool small_level(const Grid3& g, int num_sms) {
+    const long long tiles = (long long)((g.nx + S2X - 1) / S2X) * ((g.ny + S2Y - 1) / S2Y);
+    return tiles * ((g.nz + FZC - 1) / FZC) <= num_sms;
+}
+
+template <int R, int V>
+static cudaError_t launch_fs(const FusedArgs& a, cudaStream_t s) {
+    using G = S2Geom<R>;
+    using F = FSGeom<R>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    const Grid3& g = a.g;
+    const cuuint64_t vdims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t sdims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 1};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                   (cuuint64_t)g.cs * 4};
+    const cuuint32_t vbox[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, (cuuint32_t)F::NP, 3u};
+    const cuuint32_t sbox[4] = {(cuuint32_t)F2SW, (cuuint32_t)F2SH, (cuuint32_t)F::SNP, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUtensorMap vmap, smap;
+    auto enc4 = [&](CUtensorMap* m, const void* p, const cuuint64_t* d, const cuuint32_t* b) {
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(p), d, strides, b, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+               CUDA_SUCCESS;
+    };
+    if (!enc4(&vmap, a.vin, vdims, vbox) || !enc4(&smap, a.S, sdims, sbox))
+        return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            fused_small_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 grid((g.nx + S2X - 1) / S2X, (g.ny + S2Y - 1) / S2Y, (g.nz + FZC - 1) / FZC);
+    fused_small_kernel<R, V><<<grid, dim3(F2T, 1, 1), F::SMEM, s>>>(vmap, smap, a);
+    return cudaGetLastError();
+}
+
 template <int R>
 static cudaError_t launch_f2r(int variant, const FusedArgs& a, int num_sms, cudaStream_t s) {
+    if (R <= 3 && small_level(a.g, num_sms))
+        return variant == 1 ? launch_fs<R <= 3 ? R : 3, 1>(a, s) : launch_fs<R <= 3 ? R : 3, 0>(a, s);
     return variant == 1 ? launch_f2<R, 1>(a, num_sms, s) : launch_f2<R, 0>(a, num_sms, s);
 }
 

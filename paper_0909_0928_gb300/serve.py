@@ -223,7 +223,7 @@ def make_requests(n: int, rate: float, seed: int, sizes=DEFAULT_SIZES,
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rates", type=float, nargs="+", default=[1, 2, 5, 10, 20])
+    ap.add_argument("--rates", type=float, nargs="+", default=[1, 2, 5, 10, 20, 40])
     ap.add_argument("--jobs", type=int, default=30)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--seed", type=int, default=5)
