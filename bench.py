@@ -530,8 +530,10 @@ def main():
     per_variant = None
     if not args.no_variants:
         per_variant = {}
-        for vid, alpha, fuse in ((0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 0), (2, 0.4, 0), (3, 0.4, 0),
-                                 (4, 0.4, 0), (4, 2.0, 0), (5, 0.4, 0)):
+        # the library's default schedule (fuse = 2) for every force law, plus
+        # passive with the two-kernel schedule everywhere (0) and fused everywhere (1)
+        for vid, alpha, fuse in ((0, 0.4, 2), (0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 2), (2, 0.4, 2),
+                                 (3, 0.4, 2), (4, 0.4, 2), (4, 2.0, 2), (5, 0.4, 2)):
             p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, fuse=fuse)
             c2 = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, vid, p2, stream)
             ms = []
@@ -542,7 +544,7 @@ def main():
                     ms.append(st.ms_total)
             dl.dir_destroy(c2)
             name = VARIANT_NAMES[vid] + (f"_alpha{alpha}" if vid == 4 else "") + \
-                ("_fused" if fuse else "")
+                {2: "", 0: "_two_kernel", 1: "_fused_all_levels"}[fuse]
             med = statistics.median(ms)
             per_variant[name] = {"ms_p50": med, "voxel_updates_per_s": vu_step / (med / 1e3)}
 

@@ -61,15 +61,18 @@ __global__ void ic_invert_kernel(const TF* __restrict__ h, TF* __restrict__ u, G
     const TF* hx = h;
     const TF* hy = h + g.cs;
     const TF* hz = h + 2 * g.cs;
-    // x* = y + a with a = h(x*), iterated from a = 0
+    // x* = y + a with a = h(x*), iterated from a = 0; once a step returns its
+    // input exactly, every later step would too, so the loop may stop there
     Real ax = 0, ay = 0, az = 0;
     for (int s = 0; s < steps; ++s) {
         const Real nx_ = trilinear<Real>(hx, g, x, ax, y, ay, z, az);
         const Real ny_ = trilinear<Real>(hy, g, x, ax, y, ay, z, az);
         const Real nz_ = trilinear<Real>(hz, g, x, ax, y, ay, z, az);
+        const bool fixed = (nx_ == ax) && (ny_ == ay) && (nz_ == az);
         ax = nx_;
         ay = ny_;
         az = nz_;
+        if (fixed) break;
     }
     const long long o = (long long)offs(g, x, y, z);
     u[o] = st_as<TF>(Real(2) * trilinear<Real>(hx, g, x, ax, y, ay, z, az));

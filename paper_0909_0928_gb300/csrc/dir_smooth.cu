@@ -172,6 +172,159 @@ __global__ void __launch_bounds__(S2T, 8)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Field smoothing for small levels: a block of 384 threads (a group of 128
+// per component) owns a 32 x 16 tile and SZC = 2 output planes, fetches the
+// SZC + 2R input planes of all three components in one TMA copy and runs the
+// x, y and z passes over all planes at once (see the fused small-level kernel
+// in dir_fused.cu; same building blocks and order of operations as the
+// marching kernel above).
+// ---------------------------------------------------------------------------
+constexpr int SZC = 2, SST = 3 * S2T;
+
+template <int R>
+struct SSGeom {
+    using G = S2Geom<R>;
+    static constexpr int NP = SZC + 2 * R;
+    static constexpr int PLANE = G::H * G::WB;
+    static constexpr int VBOX = 3 * NP * PLANE * 4;
+    static constexpr int YPL = (S2Y / 2) * S2X;
+    static constexpr int OFF_TXP = (VBOX + 127) / 128 * 128;
+    static constexpr int OFF_BAR = OFF_TXP + 3 * NP * G::TXP_STRIDE;
+    static constexpr int SMEM = 128 + OFF_BAR + 64;
+    static_assert(3 * NP * YPL * 8 <= VBOX, "y-filtered planes reuse the plane boxes");
+};
+
+template <int R>
+__global__ void __launch_bounds__(SST, 1)
+    smooth_small_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a) {
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    using G = S2Geom<R>;
+    using F = SSGeom<R>;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB, NP = F::NP;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + F::OFF_BAR);
+    float* vbox = reinterpret_cast<float*>(base);  // [3][NP][H][WB]
+    f32x2* ypl = reinterpret_cast<f32x2*>(base);   // [3][NP][8][32], after the x pass
+    const Grid3 g = a.g;
+    float w[R + 1];
+    f32x2 wp[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+        w[t] = a.taps.wf[t];
+        wp[t] = f2_pack(w[t], w[t]);
+    }
+    const int tid = threadIdx.x;
+    const int grp = tid >> 7, gt = tid & 127;
+    const int lx = gt & 31, q = gt >> 5;
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * S2Y;
+    const int z0 = blockIdx.z * SZC;
+    const int zb = z0 - R;
+    const int bx = x0 - HA, by = y0 - R;
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
+    const int pa = max(0, -zb), pb = min(NP - 1, g.nz - 1 - zb);  // in-volume planes
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, (uint32_t)F::VBOX);
+        tma_load_4d(vbox, &tmap, bx, by, zb, 0, bar);
+    }
+    __syncthreads();
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+        return;
+    }
+    (void)mbar_try_wait(bar, 0);
+    if (edge) s2_edge_fix<R>(vbox, H * WB, 3 * NP, bx, by, g, tid, SST);
+    f32x2* txp_c = reinterpret_cast<f32x2*>(base + F::OFF_TXP) + (size_t)grp * NP * (G::TXP_STRIDE / 8);
+    for (int p = pa; p <= pb; ++p)
+        s2_xpass<R>(vbox + (grp * NP + p) * F::PLANE,
+                    reinterpret_cast<float*>(txp_c + p * (G::TXP_STRIDE / 8)), gt, w);
+    __syncthreads();
+    for (int p = pa; p <= pb; ++p) {
+        const f32x2* tp = txp_c + p * (G::TXP_STRIDE / 8);
+        f32x2 in2[K + 1];
+#pragma unroll
+        for (int m = 0; m < K + 1; ++m) in2[m] = tp[(2 * q + m) * S2TP + lx];
+        f32x2 p0 = 0ull, p1 = 0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const f32x2 wt = wp[t <= R ? t : 2 * R - t];
+            p0 = f2_fma(wt, in2[t], p0);
+            p1 = f2_fma(wt, in2[t + 1], p1);
+        }
+        f32x2* yp = ypl + (size_t)(grp * NP + p) * F::YPL;
+        yp[(2 * q) * S2X + lx] = p0;
+        yp[(2 * q + 1) * S2X + lx] = p1;
+    }
+    __syncthreads();
+    float* __restrict__ out = static_cast<float*>(a.out) + (long long)grp * g.cs;
+    const int x = x0 + lx, ya = y0 + 2 * q;
+    const int rows_left = x < g.nx ? g.ny - ya : 0;
+    const int px = (int)g.px;
+#pragma unroll
+    for (int j = 0; j < SZC; ++j) {
+        if (z0 + j >= g.nz) break;
+        f32x2 r0 = 0ull, r1 = 0ull;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const int pp = clampi(j + t, pa, pb);  // plane z0 + j - R + t, clamped
+            const f32x2* yp = ypl + (size_t)(grp * NP + pp) * F::YPL;
+            const f32x2 wt = wp[t <= R ? t : 2 * R - t];
+            r0 = f2_fma(wt, yp[(2 * q) * S2X + lx], r0);
+            r1 = f2_fma(wt, yp[(2 * q + 1) * S2X + lx], r1);
+        }
+        float a0, b0, a1, b1;
+        f2_unpack(r0, a0, b0);
+        f2_unpack(r1, a1, b1);
+        float* o = out + offs(g, x < g.nx ? x : 0, ya, z0 + j);
+        if (rows_left > 0) o[0] = a0;
+        if (rows_left > 1) o[px] = a1;
+        if (rows_left > S2Y / 2) o[(S2Y / 2) * px] = b0;
+        if (rows_left > S2Y / 2 + 1) o[(S2Y / 2 + 1) * px] = b1;
+    }
+}
+
+static bool smooth_small_level(const Grid3& g, int num_sms) {
+    const long long tiles = (long long)((g.nx + S2X - 1) / S2X) * ((g.ny + S2Y - 1) / S2Y);
+    return tiles * ((g.nz + SZC - 1) / SZC) <= num_sms;
+}
+
+template <int R>
+static cudaError_t launch_ss(const SmoothArgs& a, cudaStream_t s) {
+    using G = S2Geom<R>;
+    using F = SSGeom<R>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    const Grid3& g = a.g;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                   (cuuint64_t)g.cs * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)G::WB, (cuuint32_t)G::H, (cuuint32_t)F::NP, 3u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUtensorMap map;
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(a.in), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            smooth_small_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 grid((g.nx + S2X - 1) / S2X, (g.ny + S2Y - 1) / S2Y, (g.nz + SZC - 1) / SZC);
+    smooth_small_kernel<R><<<grid, dim3(SST, 1, 1), F::SMEM, s>>>(map, a);
+    return cudaGetLastError();
+}
+
 template <int R>
 static bool make_s2_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
     using G = S2Geom<R>;
@@ -269,6 +422,14 @@ cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStrea
         return launch_types<double, double, double>(a, num_sms, s);
     }
     if (a.in_type == kStoreF32 && a.out_type == kStoreF32) {
+        if (a.ncomp == 3 && a.zchunk == 0 && smooth_small_level(a.g, num_sms)) {
+            switch (a.taps.R) {  // small levels: all planes of a chunk at once
+                case 1: return launch_ss<1>(a, s);
+                case 2: return launch_ss<2>(a, s);
+                case 3: return launch_ss<3>(a, s);
+                default: break;
+            }
+        }
         switch (a.taps.R) {  // the packed kernel for the usual radii
             case 1: return launch_s2<1>(a, num_sms, s);
             case 2: return launch_s2<2>(a, num_sms, s);
