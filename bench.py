@@ -95,8 +95,12 @@ def measured_peak_gbs():
 # is valid only while their combined sha256 is unchanged)
 KERNEL_SOURCES = {
     "force_kernel": ["dir_force_kernel.cuh", "dir_force_law.cuh", "dir_common.cuh"],
-    "smooth2_kernel": ["dir_smooth.cu", "dir_common.cuh"],
+    "smooth2_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
     "fused_kernel": ["dir_fused.cu", "dir_stencil.cuh", "dir_force_law.cuh", "dir_common.cuh"],
+    "fused2_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
+                      "dir_force_law.cuh", "dir_common.cuh"],
+    "fused_small_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
+                           "dir_force_law.cuh", "dir_common.cuh"],
 }
 
 
@@ -509,7 +513,7 @@ def main():
     n_fine = n0
     bytes_pv = {"force": FORCE_BYTES[args.variant_id], "fused": FORCE_BYTES[args.variant_id],
                 "smooth": SMOOTH_BYTES}
-    kernel_of = {"force": "force_kernel", "fused": "fused_kernel", "smooth": "smooth2_kernel"}
+    kernel_of = {"force": "force_kernel", "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
     per_kernel = {}
     for k, (ms, n) in kt.items():
         if n:

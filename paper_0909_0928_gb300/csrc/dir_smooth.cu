@@ -74,19 +74,20 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8, TIN>::YT)
 // 32 x 16 tile over a z chunk, fed by a 6-deep ring of TMA plane copies.
 // ---------------------------------------------------------------------------
 constexpr int S2STAGES = 6;
+constexpr bool kSmoothTall = true;  // 32-row tiles on large levels
 
-template <int R>
+template <int R, int TY>
 struct S2Smem {
-    using G = S2Geom<R>;
+    using G = S2Geom<R, TY>;
     static constexpr int SMEM = 128 + S2STAGES * G::SLOT_STRIDE + G::TXP_STRIDE + 64;
 };
 
-template <int R>
-__global__ void __launch_bounds__(S2T, 8)
+template <int R, int TY>
+__global__ void __launch_bounds__(8 * TY, 16 / TY * 8)
     smooth2_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
     if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
-    using G = S2Geom<R>;
-    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB;
+    using G = S2Geom<R, TY>;
+    constexpr int K = G::K, H = G::H, HA = G::HA, WB = G::WB, NT = G::NTG;
     extern __shared__ unsigned char smem_raw[];
     // 128-byte aligned by pointer arithmetic on the shared array (keeps the
     // accesses below in the shared address space)
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(S2T, 8)
     const int tid = threadIdx.x;
     const int lx = tid & 31, q = tid >> 5;
     const int comp = blockIdx.z % a.ncomp;
-    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * S2Y;
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * TY;
     const int z0 = (blockIdx.z / a.ncomp) * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
     const int nsteps = (z1 - z0) + 2 * R;  // input planes z0-R .. z1-1+R (clamped)
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(S2T, 8)
     for (int t = 0; t < K; ++t) ring[t][0] = ring[t][1] = 0ull;
 
     const int x = x0 + lx;
-    const int ya = y0 + 2 * q;  // rows ya, ya + 1 (lane 0) and ya + 8, ya + 9 (lane 1)
+    const int ya = y0 + 2 * q;  // rows ya, ya + 1 (lane 0) and ya + TY/2, ya + TY/2 + 1 (lane 1)
     const int px = (int)g.px;
     const int rows_left = x < g.nx ? g.ny - ya : 0;  // 0: this thread stores nothing
     for (int step = 0; step < nsteps; ++step) {
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(S2T, 8)
         }
         (void)mbar_try_wait(&full[sl], parity);
         float* slot = reinterpret_cast<float*>(base + sl * G::SLOT_STRIDE);  // [H][WB]
-        if (edge) s2_edge_fix<R>(slot, G::SLOT_STRIDE / 4, 1, bx, by, g, tid, S2T);
-        s2_xpass<R>(slot, txf, tid, w);
+        if (edge) s2_edge_fix<R, TY>(slot, G::SLOT_STRIDE / 4, 1, bx, by, g, tid, NT);
+        s2_xpass<R, TY>(slot, txf, tid, w);
         __syncthreads();
         const bool emit = step >= 2 * R;
         float* o = out + offs(g, x < g.nx ? x : 0, ya, emit ? z0 + step - 2 * R : 0);
@@ -163,15 +164,14 @@ __global__ void __launch_bounds__(S2T, 8)
                 f2_unpack(r1, a1, b1);
                 if (rows_left > 0) o[0] = a0;
                 if (rows_left > 1) o[px] = a1;
-                if (rows_left > S2Y / 2) o[(S2Y / 2) * px] = b0;
-                if (rows_left > S2Y / 2 + 1) o[(S2Y / 2 + 1) * px] = b1;
+                if (rows_left > TY / 2) o[(TY / 2) * px] = b0;
+                if (rows_left > TY / 2 + 1) o[(TY / 2 + 1) * px] = b1;
             }
         })
         // no barrier here: the next step's __syncthreads_or orders this
         // step's reads of the pair rows before the next x pass rewrites them
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // Field smoothing for small levels: a block of 384 threads (a group of 128
@@ -325,9 +325,9 @@ static cudaError_t launch_ss(const SmoothArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int R>
+template <int R, int TY>
 static bool make_s2_map(CUtensorMap* map, const void* ptr, const Grid3& g, int ncomp) {
-    using G = S2Geom<R>;
+    using G = S2Geom<R, TY>;
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz,
@@ -343,9 +343,9 @@ static bool make_s2_map(CUtensorMap* map, const void* ptr, const Grid3& g, int n
 
 // z chunk for the packed kernel: the largest number of chunks that still fits
 // in one wave of resident blocks
-static int s2_zchunk(const Grid3& g, int per_sm, int num_sms, int ncomp) {
+static int s2_zchunk(const Grid3& g, int ty, int per_sm, int num_sms, int ncomp) {
     if (per_sm < 1) per_sm = 1;
-    const long long bxy = (long long)((g.nx + S2X - 1) / S2X) * ((g.ny + S2Y - 1) / S2Y) * ncomp;
+    const long long bxy = (long long)((g.nx + S2X - 1) / S2X) * ((g.ny + ty - 1) / ty) * ncomp;
     long long chunks = ((long long)per_sm * num_sms) / bxy;
     if (chunks < 1) chunks = 1;
     if (chunks > g.nz) chunks = g.nz;
@@ -353,27 +353,37 @@ static int s2_zchunk(const Grid3& g, int per_sm, int num_sms, int ncomp) {
     return zc < 1 ? 1 : zc;
 }
 
-template <int R>
+template <int R, int TY>
 static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
-    using G = S2Smem<R>;
+    using G = S2Smem<R, TY>;
     CUtensorMap map;
-    if (!make_s2_map<R>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
+    if (!make_s2_map<R, TY>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
     static bool attr_set = false;  // per instantiation
     static int per_sm = 1;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(smooth2_kernel<R>,
+        cudaError_t e = cudaFuncSetAttribute(smooth2_kernel<R, TY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth2_kernel<R>, S2T, G::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth2_kernel<R, TY>, 8 * TY,
+                                                          G::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    int zc = a.zchunk > 0 ? a.zchunk : s2_zchunk(a.g, per_sm, num_sms, a.ncomp);
+    int zc = a.zchunk > 0 ? a.zchunk : s2_zchunk(a.g, TY, per_sm, num_sms, a.ncomp);
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
-    const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + S2Y - 1) / S2Y, chunks * a.ncomp);
-    smooth2_kernel<R><<<grid, dim3(S2T, 1, 1), G::SMEM, s>>>(map, a, zc);
+    const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + TY - 1) / TY, chunks * a.ncomp);
+    smooth2_kernel<R, TY><<<grid, dim3(8 * TY, 1, 1), G::SMEM, s>>>(map, a, zc);
     return cudaGetLastError();
+}
+
+// tile height: 32 rows where the level is large enough that fewer, taller
+// tiles still fill the GPU (less y halo per output), else 16
+template <int R>
+static cudaError_t launch_s2t(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    const long long tiles32 = (long long)((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + 31) / 32) * a.ncomp;
+    if (kSmoothTall && tiles32 * a.g.nz >= 8LL * num_sms) return launch_s2<R, 32>(a, num_sms, s);
+    return launch_s2<R, S2Y>(a, num_sms, s);
 }
 
 template <typename Real, int R, typename TIN, typename TOUT>
@@ -431,10 +441,10 @@ cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStrea
             }
         }
         switch (a.taps.R) {  // the packed kernel for the usual radii
-            case 1: return launch_s2<1>(a, num_sms, s);
-            case 2: return launch_s2<2>(a, num_sms, s);
-            case 3: return launch_s2<3>(a, num_sms, s);
-            case 4: return launch_s2<4>(a, num_sms, s);
+            case 1: return launch_s2t<1>(a, num_sms, s);
+            case 2: return launch_s2t<2>(a, num_sms, s);
+            case 3: return launch_s2t<3>(a, num_sms, s);
+            case 4: return launch_s2t<4>(a, num_sms, s);
             default: return launch_types<float, float, float>(a, num_sms, s);
         }
     }

@@ -2,15 +2,17 @@
 // (Sec. 2.5 low-pass filter, applied along x, then y, then z with replicated
 // edges), shared by the smoothing kernel and the fused iteration kernel.
 //
-// Geometry: a block smooths 32 x 16 (x, y) tiles plane by plane.  Each input
+// Geometry: a block smooths 32 x TY (x, y) tiles plane by plane (TY = 16 by
+// default, 32 for the large-level smoothing kernel).  Each input
 // plane (tile + halo: H = 16 + 2R rows, WB = 32 + 2 HA columns with the x
 // start 16-byte aligned) arrives by TMA.  The x pass (scalar, 4 outputs per
 // task from 128-bit shared loads) writes its rows into a pair-interleaved
-// buffer in which row m sits beside row m + 8, so that the y and z passes run
-// on f32x2 pairs (rows y and y + 8 of one column; fma.rn.f32x2 does both
-// lanes, each rounded as the scalar FMA would be).  A group of 128 threads
-// owns one component: thread (lx, q) holds column lx and rows {2q, 2q+1,
-// 2q+8, 2q+9}, filters them in y from 64-bit shared loads, keeps the 2R+1
+// buffer in which row m sits beside row m + TY/2, so that the y and z passes
+// run on f32x2 pairs (rows y and y + TY/2 of one column; fma.rn.f32x2 does
+// both lanes, each rounded as the scalar FMA would be).  A group of 8 TY
+// threads owns one component: thread (lx, q) holds column lx and rows
+// {2q, 2q+1, 2q+TY/2, 2q+TY/2+1}, filters them in y from 64-bit shared loads,
+// keeps the 2R+1
 // most recent y-filtered planes in registers and filters them in z.  The y
 // and z steps are instantiated per ring position J (the caller switches on
 // the plane index modulo 2R+1), so the ring rotates by renaming.
@@ -28,20 +30,21 @@ namespace dirk {
 constexpr int S2X = 32, S2Y = 16, S2T = 128;
 constexpr int S2TP = S2X + 1;  // pair-row pitch in f32x2 (the pad staggers banks)
 
-template <int R>
+template <int R, int TY = S2Y>
 struct S2Geom {
     static constexpr int K = 2 * R + 1;
-    static constexpr int H = S2Y + 2 * R;                         // box rows
+    static constexpr int NTG = 8 * TY;                            // threads per component group
+    static constexpr int H = TY + 2 * R;                          // box rows
     static constexpr int HA = (R + 3) / 4 * 4;                    // x halo, 16-byte aligned start
     static constexpr int WB = S2X + 2 * HA;                       // box width
-    static constexpr int NPR = S2Y / 2 + 2 * R;                   // pair rows (m, m + 8)
+    static constexpr int NPR = TY / 2 + 2 * R;                    // pair rows (m, m + TY/2)
     static constexpr int XLV = (HA - R + 4 + 2 * R + 3) / 4 * 4;  // x-task inputs, whole float4s
     static constexpr int SLOT = H * WB * 4;                       // bytes of one plane box
     static constexpr int SLOT_STRIDE = (SLOT + 127) / 128 * 128;
     static constexpr int TXP = NPR * S2TP * 8;                    // bytes of the pair rows
     static constexpr int TXP_STRIDE = (TXP + 127) / 128 * 128;
     static constexpr int XTASKS = H * (S2X / 4);                  // x tasks per plane
-    static_assert(XTASKS > S2T && XTASKS <= 2 * S2T, "x tasks: one or two per thread");
+    static_assert(XTASKS > NTG && XTASKS <= 2 * NTG, "x tasks: one or two per thread");
 };
 
 template <int R>
@@ -51,11 +54,11 @@ __device__ __forceinline__ float s2_w(const float (&w)[R + 1], int t) {
 
 // x pass of one task: box row rho, outputs 4 gq .. 4 gq + 3, written to the
 // pair rows (as the low lane of pair row rho and the high lane of pair row
-// rho - 8, where those exist)
-template <int R>
+// rho - TY/2, where those exist)
+template <int R, int TY = S2Y>
 __device__ __forceinline__ void s2_xtask(const float* __restrict__ slot, float* __restrict__ txf,
                                          int tk, const float (&w)[R + 1]) {
-    using G = S2Geom<R>;
+    using G = S2Geom<R, TY>;
     constexpr int K = 2 * R + 1, HA = G::HA, WB = G::WB, NPR = G::NPR;
     const int gq = tk & 7, rho = tk >> 3;
     const float* src = slot + rho * WB + 4 * gq;
@@ -81,29 +84,30 @@ __device__ __forceinline__ void s2_xtask(const float* __restrict__ slot, float* 
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
     }
-    if (rho >= S2Y / 2) {
-        float* d = txf + 2 * ((rho - S2Y / 2) * S2TP + 4 * gq) + 1;
+    if (rho >= TY / 2) {
+        float* d = txf + 2 * ((rho - TY / 2) * S2TP + 4 * gq) + 1;
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) d[2 * jj] = o[jj];
     }
 }
 
-// x pass of a whole plane by the 128 threads of one group (tid in 0..127)
-template <int R>
+// x pass of a whole plane by the 8 TY threads of one group (tid in 0..8 TY-1)
+template <int R, int TY = S2Y>
 __device__ __forceinline__ void s2_xpass(const float* __restrict__ slot, float* __restrict__ txf,
                                          int tid, const float (&w)[R + 1]) {
-    s2_xtask<R>(slot, txf, tid, w);
-    if (tid < S2Geom<R>::XTASKS - S2T) s2_xtask<R>(slot, txf, tid + S2T, w);
+    using G = S2Geom<R, TY>;
+    s2_xtask<R, TY>(slot, txf, tid, w);
+    if (tid < G::XTASKS - G::NTG) s2_xtask<R, TY>(slot, txf, tid + G::NTG, w);
 }
 
 // Replicate boundary in a TMA plane box of `nc` components (zero-filled where
 // outside the volume): out-of-volume columns first (a thread per row), then
 // out-of-volume rows (a thread per column).  bx, by: box origin.  Every thread
 // of the block calls it (two barriers).
-template <int R>
+template <int R, int TY = S2Y>
 __device__ __forceinline__ void s2_edge_fix(float* slots, int slot_stride_floats, int nc, int bx,
                                             int by, const Grid3& g, int tid, int nthreads) {
-    using G = S2Geom<R>;
+    using G = S2Geom<R, TY>;
     constexpr int H = G::H, WB = G::WB;
     const int lo = max(0, -bx), hi = min(WB, g.nx - bx);
     for (int row = tid; row < nc * H; row += nthreads) {
@@ -123,8 +127,8 @@ __device__ __forceinline__ void s2_edge_fix(float* slots, int slot_stride_floats
     __syncthreads();
 }
 
-// y pass of one plane into ring slot J (pairs (2q + t, 2q + 8 + t) and
-// (2q + 1 + t, 2q + 9 + t) of the pair rows)
+// y pass of one plane into ring slot J (pair rows 2q + t and 2q + 1 + t, i.e.
+// rows (2q + t, 2q + TY/2 + t) and (2q + 1 + t, 2q + TY/2 + 1 + t))
 template <int R, int J>
 __device__ __forceinline__ void s2_y(const f32x2* __restrict__ txp, int q, int lx,
                                      const f32x2 (&wp)[R + 1], f32x2 (&ring)[2 * R + 1][2]) {
@@ -144,7 +148,7 @@ __device__ __forceinline__ void s2_y(const f32x2* __restrict__ txp, int q, int l
 }
 
 // z pass over the ring whose newest plane is in slot J, oldest plane first:
-// r0 = (row 2q, row 2q + 8), r1 = (row 2q + 1, row 2q + 9)
+// r0 = (row 2q, row 2q + TY/2), r1 = (row 2q + 1, row 2q + TY/2 + 1)
 template <int R, int J>
 __device__ __forceinline__ void s2_z(const f32x2 (&wp)[R + 1], const f32x2 (&ring)[2 * R + 1][2],
                                      f32x2& r0, f32x2& r1) {

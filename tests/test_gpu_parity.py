@@ -354,7 +354,7 @@ def test_fused_schedule_matches_two_kernel_schedule(dl, small_phantom, variant, 
     np.testing.assert_allclose(a["hist"], b["hist"], rtol=1e-5 if not fp64 else 1e-12)
 
 
-@pytest.mark.parametrize("dims", [(45, 37, 19), (70, 9, 33), (100, 60, 41)])
+@pytest.mark.parametrize("dims", [(45, 37, 19), (70, 9, 33), (100, 60, 41), (160, 150, 48)])
 def test_fused_schedule_ragged(dl, dims):
     # partial tiles in x and y, odd z chunks, three levels: the fused kernel
     # against the two-kernel schedule and the oracle
