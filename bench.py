@@ -95,6 +95,8 @@ def measured_peak_gbs():
 # is valid only while their combined sha256 is unchanged)
 KERNEL_SOURCES = {
     "force_kernel": ["dir_force_kernel.cuh", "dir_force_law.cuh", "dir_common.cuh"],
+    "force_tma_kernel": ["dir_force_tma.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
+                         "dir_stencil.cuh", "dir_common.cuh"],
     "smooth2_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
     "fused_kernel": ["dir_fused.cu", "dir_stencil.cuh", "dir_force_law.cuh", "dir_common.cuh"],
     "fused2_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
@@ -513,7 +515,8 @@ def main():
     n_fine = n0
     bytes_pv = {"force": FORCE_BYTES[args.variant_id], "fused": FORCE_BYTES[args.variant_id],
                 "smooth": SMOOTH_BYTES}
-    kernel_of = {"force": "force_kernel", "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
+    kernel_of = {"force": "force_tma_kernel" if args.variant_id in (0, 1) else "force_kernel",
+                 "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
     per_kernel = {}
     for k, (ms, n) in kt.items():
         if n:

@@ -50,6 +50,16 @@ __device__ __forceinline__ int offs(const Grid3& g, int i, int j, int k) {
     return i + g.px * j + (int)g.plane * k;
 }
 
+// Fused multiply-add written out: every kernel that evaluates the same formula
+// then rounds it the same way (the compiler's own contraction of a * b + c
+// may pick a different product to fuse in different kernels).
+__device__ __forceinline__ float r_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double r_fma(double a, double b, double c) { return fma(a, b, c); }
+// |(x, y, z)|^2 as ((x x) + y y) + z z with the two additions fused
+template <typename Real>
+__device__ __forceinline__ Real r_sq3(Real x, Real y, Real z) {
+    return r_fma(z, z, r_fma(y, y, x * x));
+}
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float r_floor(float x) { return floorf(x); }
@@ -138,13 +148,13 @@ __device__ __forceinline__ Real trilinear(const T* __restrict__ I, const Grid3& 
     const Real c001 = ldg_as<Real>(p01 + x0) - ref, c101 = ldg_as<Real>(p01 + x1) - ref;
     const Real c011 = ldg_as<Real>(p11 + x0) - ref, c111 = ldg_as<Real>(p11 + x1) - ref;
     const Real gx = Real(1) - fx, gy = Real(1) - fy, gz = Real(1) - fz;
-    const Real v00 = c000 * gx + c100 * fx;
-    const Real v10 = c010 * gx + c110 * fx;
-    const Real v01 = c001 * gx + c101 * fx;
-    const Real v11 = c011 * gx + c111 * fx;
-    const Real v0 = v00 * gy + v10 * fy;
-    const Real v1 = v01 * gy + v11 * fy;
-    return v0 * gz + v1 * fz;
+    const Real v00 = r_fma(c100, fx, c000 * gx);
+    const Real v10 = r_fma(c110, fx, c010 * gx);
+    const Real v01 = r_fma(c101, fx, c001 * gx);
+    const Real v11 = r_fma(c111, fx, c011 * gx);
+    const Real v0 = r_fma(v10, fy, v00 * gy);
+    const Real v1 = r_fma(v11, fy, v01 * gy);
+    return r_fma(v1, fz, v0 * gz);
 }
 
 // Block-wide sum of three per-thread partial sums, then one FP64 atomic per

@@ -303,6 +303,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.stop_iter = c->ctl + lc;
         fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms, 4);
         fa.pf_stride = 4 * c->num_sms;  // one wave of force blocks (4 per SM)
+        fa.err = c->derr;
         fa.img_type = c->img_type(l);
         fa.field_type = c->field_type;
         dirk::SmoothArgs sa;
@@ -1062,6 +1063,7 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         fa.iter = 0;
         fa.img_type = c->img_type(l);
         fa.field_type = c->field_type;
+        fa.err = c->derr;
         float best = 1e30f;
         int best_d = 0;
         for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {

@@ -19,10 +19,18 @@ cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_
         if (a.img_type != kStoreF64 || a.field_type != kStoreF64) return cudaErrorInvalidValue;
         return launch_force_f64(variant, a, s);
     }
-    if (a.img_type == kStoreI16) return launch_force_i16(variant, a, s);
+    if (a.img_type == kStoreI16) {
+        const cudaError_t e = launch_force_tma(variant, a, s);  // Eqs. 1-2: TMA-fed bricks
+        if (e != cudaErrorNotSupported) return e;
+        return launch_force_i16(variant, a, s);
+    }
     if (a.img_type != kStoreF32) return cudaErrorInvalidValue;
     if (a.field_type == kStoreBF16) return launch_force_bf16(variant, a, s);
-    if (a.field_type == kStoreF32) return launch_force_f32(variant, a, s);
+    if (a.field_type == kStoreF32) {
+        const cudaError_t e = launch_force_tma(variant, a, s);  // Eqs. 1-2: TMA-fed bricks
+        if (e != cudaErrorNotSupported) return e;
+        return launch_force_f32(variant, a, s);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -88,13 +88,13 @@ __device__ __forceinline__ Real interp_rel(const T* __restrict__ I, const Interp
     const Real c001 = ldg_as<Real>(p2) - ref, c101 = ldg_as<Real>(p2 + 1) - ref;
     const Real c011 = ldg_as<Real>(p3) - ref, c111 = ldg_as<Real>(p3 + 1) - ref;
     const Real gx = Real(1) - fx, gy = Real(1) - fy, gz = Real(1) - fz;
-    const Real v00 = c000 * gx + c100 * fx;
-    const Real v10 = c010 * gx + c110 * fx;
-    const Real v01 = c001 * gx + c101 * fx;
-    const Real v11 = c011 * gx + c111 * fx;
-    const Real v0 = v00 * gy + v10 * fy;
-    const Real v1 = v01 * gy + v11 * fy;
-    return v0 * gz + v1 * fz;
+    const Real v00 = r_fma(c100, fx, c000 * gx);
+    const Real v10 = r_fma(c110, fx, c010 * gx);
+    const Real v01 = r_fma(c101, fx, c001 * gx);
+    const Real v11 = r_fma(c111, fx, c011 * gx);
+    const Real v0 = r_fma(v10, fy, v00 * gy);
+    const Real v1 = r_fma(v11, fy, v01 * gy);
+    return r_fma(v1, fz, v0 * gz);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
                 if constexpr (T::GM) {
                     // grad W = grad D + grad S (Eq. 6: grad(W_m + W_s) = grad(D_m + D_s) + 2 grad S)
                     const Real ns = T::IC ? Real(2) : Real(1);
-                    gmx = Real(0.5) * (Wt[k + 1][ty + 1][tx + 2] - Wt[k + 1][ty + 1][tx]) + ns * gsx;
-                    gmy = Real(0.5) * (Wt[k + 1][ty + 2][tx + 1] - Wt[k + 1][ty][tx + 1]) + ns * gsy;
-                    gmz = Real(0.5) * (Wt[k + 2][ty + 1][tx + 1] - Wt[k][ty + 1][tx + 1]) + ns * gsz;
+                    gmx = r_fma(ns, gsx, Real(0.5) * (Wt[k + 1][ty + 1][tx + 2] - Wt[k + 1][ty + 1][tx]));
+                    gmy = r_fma(ns, gsy, Real(0.5) * (Wt[k + 1][ty + 2][tx + 1] - Wt[k + 1][ty][tx + 1]));
+                    gmz = r_fma(ns, gsz, Real(0.5) * (Wt[k + 2][ty + 1][tx + 1] - Wt[k][ty + 1][tx + 1]));
                     if (T::IC)
                         d = Dt[T::IC ? k : 0][ty][tx];
                     else
@@ -286,6 +286,7 @@ static cudaError_t launch_force_types(int variant, const ForceArgs& a, cudaStrea
 }
 
 // one per translation unit
+cudaError_t launch_force_tma(int variant, const ForceArgs& a, cudaStream_t s);   // Eqs. 1-2, f32
 cudaError_t launch_force_f32(int variant, const ForceArgs& a, cudaStream_t s);   // f32 / f32
 cudaError_t launch_force_f64(int variant, const ForceArgs& a, cudaStream_t s);   // f64 / f64
 cudaError_t launch_force_i16(int variant, const ForceArgs& a, cudaStream_t s);   // i16 / f32, i16 / bf16

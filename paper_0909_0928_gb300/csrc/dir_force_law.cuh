@@ -25,14 +25,16 @@ template <typename Real, int V>
 __device__ __forceinline__ void demons_force(Real d, Real gsx, Real gsy, Real gsz, Real gmx,
                                              Real gmy, Real gmz, Real b, Real alpha2, Real& dx,
                                              Real& dy, Real& dz) {
+    // every a * b + c below is an explicit fused multiply-add (r_fma, r_sq3), so
+    // that all kernels round the force identically
     const Real d2 = d * d;
     if (V == 0) {
-        term(d, gsx, gsy, gsz, d2 + (gsx * gsx + gsy * gsy + gsz * gsz), dx, dy, dz);
+        term(d, gsx, gsy, gsz, d2 + r_sq3(gsx, gsy, gsz), dx, dy, dz);
     } else if (V == 1) {
-        const Real gs2 = gsx * gsx + gsy * gsy + gsz * gsz;
+        const Real gs2 = r_sq3(gsx, gsy, gsz);
         const Real a = r_sqrt(gs2);
-        const Real s = a * a + b * b;
-        const Real den = (Real(2) * d2 + s) * s;
+        const Real s = r_fma(b, b, a * a);
+        const Real den = r_fma(Real(2), d2, s) * s;
         if (den == Real(0)) {
             dx = dy = dz = Real(0);
         } else {
@@ -42,12 +44,12 @@ __device__ __forceinline__ void demons_force(Real d, Real gsx, Real gsy, Real gs
             dz = c * gsz;
         }
     } else if (V == 2 || V == 5) {
-        term(d, gmx, gmy, gmz, d2 + (gmx * gmx + gmy * gmy + gmz * gmz), dx, dy, dz);
+        term(d, gmx, gmy, gmz, d2 + r_sq3(gmx, gmy, gmz), dx, dy, dz);
     } else {
         const Real ad2 = (V == 4) ? alpha2 * d2 : d2;
         Real px, py, pz, qx, qy, qz;
-        term(d, gsx, gsy, gsz, ad2 + (gsx * gsx + gsy * gsy + gsz * gsz), px, py, pz);
-        term(d, gmx, gmy, gmz, ad2 + (gmx * gmx + gmy * gmy + gmz * gmz), qx, qy, qz);
+        term(d, gsx, gsy, gsz, ad2 + r_sq3(gsx, gsy, gsz), px, py, pz);
+        term(d, gmx, gmy, gmz, ad2 + r_sq3(gmx, gmy, gmz), qx, qy, qz);
         dx = px + qx;
         dy = py + qy;
         dz = pz + qz;

@@ -31,6 +31,7 @@ struct ForceArgs {
     int field_type;      // storage of u and v (kStore*)
     int pf_stride = 0;   // > 0: each block prefetches into L2 the brick of the block
                          // this many linear indices ahead (about one wave)
+    int* err = nullptr;  // device error word (kErr* bits) for bounded waits
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
 int force_brick_depth(const Grid3& g, int num_sms, int waves);
