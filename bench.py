@@ -97,6 +97,8 @@ KERNEL_SOURCES = {
     "force_kernel": ["dir_force_kernel.cuh", "dir_force_law.cuh", "dir_common.cuh"],
     "force_tma_kernel": ["dir_force_tma.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
                          "dir_stencil.cuh", "dir_common.cuh"],
+    "force_tma_gm_kernel": ["dir_force_tma.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
+                            "dir_stencil.cuh", "dir_common.cuh"],
     "smooth2_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
     "fused_kernel": ["dir_fused.cu", "dir_stencil.cuh", "dir_force_law.cuh", "dir_common.cuh"],
     "fused2_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
@@ -359,7 +361,9 @@ def landmark_error_mm(u_vox, landmarks, u_true_mm, spacing):
 def run_study(args):
     """Accuracy studies on the full-size phantom with its known deformation
     (Sec. 3.2 evaluation on synthetic landmarks): every force law, the alpha
-    of Eq. (5) from 0.1 to 5, and the relative-norm stop test of Sec. 2.4."""
+    of Eq. (5) from 0.1 to 5, the relative-norm stop test of Sec. 2.4, and the
+    finest level iteration by iteration, each with the correlation of the
+    deformed moving image with S beside the landmark error (Sec. 3.3)."""
     import numpy as np
     import torch
     import paper_0909_0928_gb300 as dl
@@ -374,26 +378,43 @@ def run_study(args):
            "landmarks": int(lm.shape[0]),
            "initial_mm": {"mean": float(init.mean()), "sd": float(init.std())}}
 
-    def run(variant, alpha=0.4, stop_mode=0, eps=1e-4):
-        p = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, stop_mode=stop_mode,
-                                  eps=eps, stop_window=10)
+    S_np = ph["S"].astype(np.float64)
+
+    def correlation(W):
+        """Pearson correlation of the deformed moving image with S (the image
+        similarity the paper contrasts with spatial accuracy, Sec. 3.3)."""
+        a = S_np - S_np.mean()
+        b = W.astype(np.float64) - W.mean()
+        return float((a * b).sum() / np.sqrt((a * a).sum() * (b * b).sum()))
+
+    def run(variant, alpha=0.4, stop_mode=0, eps=1e-4, iters=ITERS, reps=3):
+        p = dl.dir_params_default(levels=LEVELS, iters=list(iters), alpha=alpha,
+                                  stop_mode=stop_mode, eps=eps, stop_window=10)
         ctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, variant, p, stream)
         try:
             st = dl.dir_register(ctx)
-            ms = [dl.dir_register(ctx).ms_total for _ in range(3)]
+            ms = [dl.dir_register(ctx).ms_total for _ in range(reps)]
             u = np.empty((3,) + ph["S"].shape, np.float32)
             dl.dir_get_field(ctx, u)
+            W = np.empty(ph["S"].shape, np.float32)
+            dl.dir_warp(ctx, ph["M"], W)
         finally:
             dl.dir_destroy(ctx)
         m, sd = landmark_error_mm(u, lm, ut, SPACING)
-        return {"landmark_mm": {"mean": m, "sd": sd}, "ms": statistics.median(ms),
-                "iters_run": list(st.iters_run[:LEVELS]), "mse_final": st.mse_final}
+        return {"landmark_mm": {"mean": m, "sd": sd}, "ms": statistics.median(ms) if ms else None,
+                "iters_run": list(st.iters_run[:LEVELS]), "mse_final": st.mse_final,
+                "relnorm_final": st.relnorm_final, "correlation": correlation(W)}
 
     out["variants"] = {VARIANT_NAMES[v]: run(v) for v in range(6)}
     out["alpha_sweep_adjusted_double"] = {str(a): run(4, alpha=a)
-                                          for a in (0.1, 0.2, 0.4, 1.0, 2.0, 5.0)}
+                                          for a in (0.1, 0.2, 0.4, 0.5, 1.0, 2.0, 3.0, 5.0)}
     out["stop_test_passive"] = {f"{e:g}": run(0, stop_mode=1, eps=e)
                                 for e in (1e-2, 1e-3, 1e-4, 1e-5)}
+    # the finest level iteration by iteration (Fig. 3a): a registration stopped
+    # after k finest iterations is the state of iteration k of a longer one
+    out["finest_iterations_passive"] = {
+        str(k): run(0, iters=[ITERS[0], ITERS[1], k], reps=0)
+        for k in (0, 5, 10, 20, 30, 50, 70, 90)}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -411,7 +432,7 @@ def main():
     ap.add_argument("--form", default="plain", choices=["plain", "batch", "study"])
     ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2],
                     help="fold the Gaussian into the next force pass (Eqs. 1-2): 0 never, "
-                         "1 every level, 2 (library default) levels up to 2M voxels")
+                         "1 every level, 2 (library default) the small levels")
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
@@ -515,7 +536,7 @@ def main():
     n_fine = n0
     bytes_pv = {"force": FORCE_BYTES[args.variant_id], "fused": FORCE_BYTES[args.variant_id],
                 "smooth": SMOOTH_BYTES}
-    kernel_of = {"force": "force_tma_kernel" if args.variant_id in (0, 1) else "force_kernel",
+    kernel_of = {"force": "force_tma_kernel" if args.variant_id in (0, 1) else "force_tma_gm_kernel",
                  "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
     per_kernel = {}
     for k, (ms, n) in kt.items():

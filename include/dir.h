@@ -93,8 +93,9 @@ typedef struct {
     int fuse;                    /* for Eqs. (1)-(2) without the stop test, with FP32 images and
                                     field: fold the Gaussian of iteration k into the force pass of
                                     iteration k+1 (same arithmetic, one pass over the field per
-                                    iteration).  0: never; 1: every level; 2 (default): levels of
-                                    at most 2,000,000 voxels, where it is faster */
+                                    iteration).  0: never; 1: every level; 2 (default): the small
+                                    levels that one block per SM covers in two-plane chunks
+                                    (e.g. 64 x 64 x 25), where it is faster */
 } dir_params;
 
 typedef struct {

@@ -34,11 +34,6 @@ namespace {
 constexpr int kIcInvertSteps = 20;
 constexpr int kStopUnset = 0x7f7f7f7f;  // memset byte 0x7f
 
-// fuse = 2: levels up to this many voxels use the fused iteration (there the
-// smaller number of launches and passes wins; on larger levels the two-kernel
-// schedule keeps more blocks in flight)
-constexpr long long kFuseAutoVoxels = 2000000;
-
 thread_local std::string g_create_error;
 
 long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -301,7 +296,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         fa.g = g;
         fa.alpha2 = c->p.alpha * c->p.alpha;
         fa.stop_iter = c->ctl + lc;
-        fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms, 4);
+        fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms);
         fa.pf_stride = 4 * c->num_sms;  // one wave of force blocks (4 per SM)
         fa.err = c->derr;
         fa.img_type = c->img_type(l);
@@ -317,8 +312,11 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         sa.zchunk = c->tune_zchunk[l];
         const bool timed = c->p.timing && l == 0;
         const int n = c->p.iters[lc];
-        const long long nvox = (long long)g.nx * g.ny * g.nz;
-        const bool fuse_here = c->p.fuse == 1 || (c->p.fuse == 2 && nvox <= kFuseAutoVoxels);
+        // fuse = 2: only the small levels, where the fused iteration's single
+        // copy per block beats two launches; on larger levels the two-kernel
+        // schedule keeps more blocks in flight (measured on 256x256x100)
+        const bool fuse_here =
+            c->p.fuse == 1 || (c->p.fuse == 2 && dirk::fused_small_level(g, c->num_sms));
         const bool fused = fuse_here && c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
                            c->field_type == c->real_type && c->img_type(l) == c->real_type;
         if (fused && n > 0) {

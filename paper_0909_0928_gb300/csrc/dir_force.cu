@@ -4,13 +4,14 @@
 
 namespace dirk {
 
-// Brick depth: the deepest of 8, 4, 2, 1 that still gives at least `waves`
-// waves of resident blocks (4 per SM), so small levels spread over the GPU.
-int force_brick_depth(const Grid3& g, int num_sms, int waves) {
+// Brick depth: the deepest of 8, 4, 2, 1 that still gives at least
+// min_blocks blocks.  The TMA-fed force kernels fetch a whole brick per copy,
+// so deeper bricks (fewer, longer blocks) pay off down to about one block per
+// SM (measured with dir_autotune on the 256x256x100 pyramid).
+int force_brick_depth(const Grid3& g, int min_blocks) {
     const long long bxy = (long long)((g.nx + FTX - 1) / FTX) * ((g.ny + FTY - 1) / FTY);
-    const long long want = (long long)waves * 4 * num_sms;
     for (int d = 8; d > 1; d /= 2)
-        if (bxy * ((g.nz + d - 1) / d) >= want) return d;
+        if (bxy * ((g.nz + d - 1) / d) >= min_blocks) return d;
     return 1;
 }
 

@@ -1,6 +1,6 @@
-// dir_force_tma.cu -- the force pass of Eqs. (1)-(2) (passive and evolved
-// passive; no gradient of the warped image), single precision, with its
-// streamed operands brought in by TMA.
+// dir_force_tma.cu -- the force pass of Eqs. (1)-(6) in single precision with
+// its streamed operands brought in by TMA (Eqs. 1-2 below; Eqs. 3-6, which
+// need the gradient of the warped image, in force_tma_gm_kernel further down).
 //
 // Same work per voxel as force_kernel (dir_force_kernel.cuh: interp_rel,
 // demons_force, the same reductions) on the same 32 x 8 x FTZ bricks, but the
@@ -197,6 +197,227 @@ static cudaError_t launch_ft(const ForceArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Eqs. (3)-(6): the force needs the gradient of the warped image, so the block
+// first forms D = W - S (Eq. 6: D_m + D_s, and d = D_m - D_s on the brick) on
+// the brick plus a one-voxel halo in shared memory, as force_kernel does, but
+// reads u (with its halo) and S from TMA boxes instead of global memory.  The
+// brick depth is at most 4 so that four blocks fit per SM.
+// ---------------------------------------------------------------------------
+template <int FTZ, int V, typename TI>
+struct FGGeom {
+    static constexpr bool IC = (V == 5);
+    static constexpr int FBX = 16 / (int)sizeof(TI);
+    static constexpr int FSW = FTX + 2 * FBX;
+    static constexpr int UW = FTX + 8, UH = FTY + 2, UD = FTZ + 2;  // u box: x0-4 .. x0+35
+    static constexpr int UBOX = 3 * UD * UH * UW * 4;             // [3][UD][UH][UW] floats
+    static constexpr int SBOX = UD * FSH * FSW * (int)sizeof(TI);  // [UD][FSH][FSW]
+    static constexpr int HX = FTX + 2, HY = FTY + 2, HZ = FTZ + 2;
+    static constexpr int WT = HZ * HY * HX * 4;                    // D on brick + halo
+    static constexpr int DT = IC ? FTZ * FTY * FTX * 4 : 0;        // Eq. 6: d on the brick
+    static constexpr int OFF_S = (UBOX + 127) / 128 * 128;
+    static constexpr int OFF_W = OFF_S + (SBOX + 127) / 128 * 128;
+    static constexpr int OFF_D = OFF_W + (WT + 127) / 128 * 128;
+    static constexpr int OFF_BAR = OFF_D + (DT + 127) / 128 * 128;
+    static constexpr int SMEM = 128 + OFF_BAR + 64;
+};
+
+template <int V, int FTZ, typename TI>
+__global__ void __launch_bounds__(FNT, 4)
+    force_tma_gm_kernel(const __grid_constant__ CUtensorMap umap,
+                        const __grid_constant__ CUtensorMap smap,
+                        const __grid_constant__ CUtensorMap mmap, const ForceArgs a) {
+    static_assert(V >= 2 && V <= 5, "Eqs. 3-6");
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;  // uniform across the grid
+    using F = FGGeom<FTZ, V, TI>;
+    constexpr int FBX = F::FBX, FSW = F::FSW, UW = F::UW, UH = F::UH, UD = F::UD;
+    constexpr int HX = F::HX, HY = F::HY, HZ = F::HZ;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const float* ub = reinterpret_cast<const float*>(base);       // [3][UD][UH][UW]
+    const TI* sb = reinterpret_cast<const TI*>(base + F::OFF_S);  // [UD][FSH][FSW]
+    float* wt = reinterpret_cast<float*>(base + F::OFF_W);        // [HZ][HY][HX]
+    float* dt = reinterpret_cast<float*>(base + F::OFF_D);        // [FTZ][FTY][FTX] (Eq. 6)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + F::OFF_BAR);
+    const Grid3 g = a.g;
+    const TI* __restrict__ S = static_cast<const TI*>(a.S);
+    const TI* __restrict__ M = static_cast<const TI*>(a.M);
+    float* __restrict__ v = static_cast<float*>(a.v);
+    const float alpha2 = (float)a.alpha2;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + FTX * ty;
+    const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
+    const int ux0 = bx0 - 4, uy0 = by0 - 1, uz0 = bz0 - 1;     // u box origin
+    const int sx0 = bx0 - FBX, sy0 = by0 - 1, sz0 = bz0 - 1;   // S box origin
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, (uint32_t)(F::UBOX + F::SBOX));
+        tma_load_4d(base, &umap, ux0, uy0, uz0, 0, bar);
+        tma_load_4d(base + F::OFF_S, &smap, sx0, sy0, sz0, 0, bar);
+        if (a.pf_stride > 0) {  // the block one wave ahead: its boxes into L2
+            const long long gx = gridDim.x, gy = gridDim.y;
+            const long long b = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) +
+                                a.pf_stride;
+            if (b < gx * gy * gridDim.z) {
+                const int px = (int)(b % gx) * FTX, py = (int)((b / gx) % gy) * FTY;
+                const int pz = (int)(b / (gx * gy)) * FTZ;
+                tma_prefetch_4d(&umap, px - 4, py - 1, pz - 1, 0);
+                tma_prefetch_4d(&smap, px - FBX, py - 1, pz - 1, 0);
+                tma_prefetch_4d(&mmap, px - FBX, py - 1, pz - 1, 0);
+            }
+        }
+    }
+    __syncthreads();
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+        return;
+    }
+    (void)mbar_try_wait(bar, 0);
+    const Interp ip(g);
+    constexpr int UC = UD * UH * UW;  // floats per u component in the box
+
+    // D on the brick plus a one-voxel halo (clamped positions; all inside the boxes)
+    for (int q = tid; q < HX * HY * HZ; q += FNT) {
+        const int hz = q / (HX * HY);
+        const int r = q - hz * (HX * HY);
+        const int hy = r / HX, hx = r - hy * HX;
+        const int gx = clampi(bx0 + hx - 1, 0, g.nx - 1);
+        const int gy = clampi(by0 + hy - 1, 0, g.ny - 1);
+        const int gz = clampi(bz0 + hz - 1, 0, g.nz - 1);
+        const int ui = ((gz - uz0) * UH + (gy - uy0)) * UW + (gx - ux0);
+        const float ux = ub[ui], uy = ub[ui + UC], uz = ub[ui + 2 * UC];
+        const float sref = (float)sb[((gz - sz0) * FSH + (gy - sy0)) * FSW + (gx - sx0)];
+        const float wm = interp_rel(M, ip, gx, ux, gy, uy, gz, uz, sref);
+        if (F::IC) {
+            const float ws = interp_rel(S, ip, gx, -ux, gy, -uy, gz, -uz, sref);
+            wt[q] = wm + ws;
+            if (hx >= 1 && hx <= FTX && hy >= 1 && hy <= FTY && hz >= 1 && hz <= FTZ)
+                dt[((hz - 1) * FTY + (hy - 1)) * FTX + (hx - 1)] = wm - ws;
+        } else {
+            wt[q] = wm;
+        }
+    }
+    __syncthreads();
+
+    const int x = bx0 + tx, y = by0 + ty;
+    const bool col_valid = (x < g.nx) && (y < g.ny);
+    const int xc = min(x, g.nx - 1), yc = min(y, g.ny - 1);
+    const int sx = xc - sx0, sxm = max(xc - 1, 0) - sx0, sxp = min(xc + 1, g.nx - 1) - sx0;
+    const int sy = yc - sy0, sym = max(yc - 1, 0) - sy0, syp = min(yc + 1, g.ny - 1) - sy0;
+    const int cs = (int)g.cs;
+    float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    if (col_valid) {
+#pragma unroll
+        for (int k = 0; k < FTZ; ++k) {
+            const int z = bz0 + k;
+            if (z < g.nz) {
+                const int pc = k + 1;
+                const int pm = max(z - 1, 0) - sz0, pp = min(z + 1, g.nz - 1) - sz0;
+                const TI* Sc = sb + pc * (FSH * FSW);
+                const float gsx = 0.5f * ((float)Sc[sy * FSW + sxp] - (float)Sc[sy * FSW + sxm]);
+                const float gsy = 0.5f * ((float)Sc[syp * FSW + sx] - (float)Sc[sym * FSW + sx]);
+                const float gsz = 0.5f * ((float)sb[pp * (FSH * FSW) + sy * FSW + sx] -
+                                          (float)sb[pm * (FSH * FSW) + sy * FSW + sx]);
+                // grad W = grad D + grad S (Eq. 6: grad(D_m + D_s) + 2 grad S), with
+                // the tile's clamped neighbours as in force_kernel
+                const float ns = F::IC ? 2.0f : 1.0f;
+                const float* W1 = wt + ((k + 1) * HY + (ty + 1)) * HX + (tx + 1);
+                const float gmx = r_fma(ns, gsx, 0.5f * (W1[1] - W1[-1]));
+                const float gmy = r_fma(ns, gsy, 0.5f * (W1[HX] - W1[-HX]));
+                const float gmz = r_fma(ns, gsz, 0.5f * (W1[HX * HY] - W1[-HX * HY]));
+                const float d = F::IC ? dt[(k * FTY + ty) * FTX + tx] : W1[0];
+                const int ui = (((k + 1) * UH) + (ty + 1)) * UW + (tx + 4);
+                const float ux = ub[ui], uy = ub[ui + UC], uz = ub[ui + 2 * UC];
+                float dx, dy, dz;
+                demons_force<float, V>(d, gsx, gsy, gsz, gmx, gmy, gmz, 0.0f, alpha2, dx, dy, dz);
+                dx = -dx;
+                dy = -dy;
+                dz = -dz;
+                sd2 += d * d;
+                sdu += r_norm_fast(dx * dx + dy * dy + dz * dz);
+                su += r_norm_fast(ux * ux + uy * uy + uz * uz);
+                const int o = offs(g, x, y, z);
+                v[o] = ux + dx;
+                v[o + cs] = uy + dy;
+                v[o + 2 * cs] = uz + dz;
+            }
+        }
+    }
+    block_reduce3_atomic<FNT, float>(sd2, sdu, su, a.red);
+}
+
+template <typename TI>
+static bool make_gm_maps(CUtensorMap* umap, CUtensorMap* smap, CUtensorMap* mmap,
+                         const ForceArgs& a, int ftz) {
+    constexpr int FSW = FTGeom<1, 0, TI>::FSW;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const Grid3& g = a.g;
+    const cuuint64_t udims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t idims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 1};
+    const cuuint64_t ustr[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                (cuuint64_t)g.cs * 4};
+    const cuuint64_t istr[3] = {(cuuint64_t)g.px * sizeof(TI), (cuuint64_t)g.plane * sizeof(TI),
+                                (cuuint64_t)g.cs * sizeof(TI)};
+    const cuuint32_t ubox[4] = {(cuuint32_t)(FTX + 8), (cuuint32_t)(FTY + 2), (cuuint32_t)(ftz + 2),
+                                3u};
+    const cuuint32_t ibox[4] = {(cuuint32_t)FSW, (cuuint32_t)FSH, (cuuint32_t)(ftz + 2), 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    auto enc4 = [&](CUtensorMap* m, CUtensorMapDataType t, const void* p, const cuuint64_t* d,
+                    const cuuint64_t* st, const cuuint32_t* b) {
+        return enc(m, t, 4, const_cast<void*>(p), d, st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    return enc4(umap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.u, udims, ustr, ubox) &&
+           enc4(smap, tma_type<TI>(), a.S, idims, istr, ibox) &&
+           enc4(mmap, tma_type<TI>(), a.M, idims, istr, ibox);
+}
+
+template <int V, int FTZ, typename TI>
+static cudaError_t launch_fg(const ForceArgs& a, cudaStream_t s) {
+    using F = FGGeom<FTZ, V, TI>;
+    CUtensorMap umap, smap, mmap;
+    if (!make_gm_maps<TI>(&umap, &smap, &mmap, a, FTZ)) return cudaErrorInvalidValue;
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(force_tma_gm_kernel<V, FTZ, TI>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   F::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
+    force_tma_gm_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), F::SMEM, s>>>(umap, smap, mmap, a);
+    return cudaGetLastError();
+}
+
+template <int V, typename TI>
+static cudaError_t launch_fg_depth(const ForceArgs& a, cudaStream_t s) {
+    switch (a.depth) {
+        case 8:
+        case 4: return launch_fg<V, 4, TI>(a, s);  // at most 4 deep (four blocks per SM)
+        case 2: return launch_fg<V, 2, TI>(a, s);
+        case 1: return launch_fg<V, 1, TI>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TI>
+static cudaError_t launch_fg_types(int variant, const ForceArgs& a, cudaStream_t s) {
+    switch (variant) {
+        case 2: return launch_fg_depth<2, TI>(a, s);
+        case 3: return launch_fg_depth<3, TI>(a, s);
+        case 4: return launch_fg_depth<4, TI>(a, s);
+        case 5: return launch_fg_depth<5, TI>(a, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 template <typename TI>
 static cudaError_t launch_ft_types(int variant, const ForceArgs& a, cudaStream_t s) {
     switch (a.depth) {
@@ -208,12 +429,17 @@ static cudaError_t launch_ft_types(int variant, const ForceArgs& a, cudaStream_t
     }
 }
 
-// Eqs. (1)-(2) in single precision with a float field and float or int16
+// Eqs. (1)-(6) in single precision with a float field and float or int16
 // images; returns cudaErrorNotSupported for anything else (the caller then
 // uses force_kernel)
 cudaError_t launch_force_tma(int variant, const ForceArgs& a, cudaStream_t s) {
-    if (variant != 0 && variant != 1) return cudaErrorNotSupported;
+    if (variant < 0 || variant > 5) return cudaErrorNotSupported;
     if (a.field_type != kStoreF32) return cudaErrorNotSupported;
+    if (variant >= 2) {
+        if (a.img_type == kStoreF32) return launch_fg_types<float>(variant, a, s);
+        if (a.img_type == kStoreI16) return launch_fg_types<int16_t>(variant, a, s);
+        return cudaErrorNotSupported;
+    }
     if (a.img_type == kStoreF32) return launch_ft_types<float>(variant, a, s);
     if (a.img_type == kStoreI16) return launch_ft_types<int16_t>(variant, a, s);
     return cudaErrorNotSupported;

@@ -670,6 +670,8 @@ static cudaError_t launch_f2r(int variant, const FusedArgs& a, int num_sms, cuda
 
 bool fused_supported(int variant) { return variant == 0 || variant == 1; }
 
+bool fused_small_level(const Grid3& g, int num_sms) { return small_level(g, num_sms); }
+
 cudaError_t launch_fused(int variant, bool fp64, const FusedArgs& a, int num_sms, cudaStream_t s) {
     if (!fused_supported(variant)) return cudaErrorInvalidValue;
     if (fp64) return launch_t<double>(variant, a, num_sms, s);

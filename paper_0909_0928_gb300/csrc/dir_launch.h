@@ -34,7 +34,7 @@ struct ForceArgs {
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
-int force_brick_depth(const Grid3& g, int num_sms, int waves);
+int force_brick_depth(const Grid3& g, int min_blocks);
 
 // Separable Gaussian (Sec. 2.5 low-pass filter), x then y then z, replicate
 // edges, ncomp components cs apart, fed by TMA.  Skips when *stop_iter < iter.
@@ -68,6 +68,9 @@ struct FusedArgs {
     int* err;
 };
 bool fused_supported(int variant);
+// the level is small enough for the all-planes-at-once fused kernel (one block
+// per SM covers it); there the fused iteration beats the two-kernel schedule
+bool fused_small_level(const Grid3& g, int num_sms);
 cudaError_t launch_fused(int variant, bool fp64, const FusedArgs& a, int num_sms, cudaStream_t s);
 
 // out(i, j, k) = in(2i, 2j, 2k)   (pyramid decimation, Sec. 2.3; float or double)
