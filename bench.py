@@ -11,6 +11,7 @@ second of device time) with s per registration p50/p99 beside it.
   python bench.py --impl reference   # FP64 CPU oracle on the host cores
   python bench.py --form batch       # 32 uneven int16 pairs: one graph vs 32 plain runs
   python bench.py --form study       # landmark accuracy per force law, alpha sweep, stop test
+  python bench.py --form precision   # int16 images / BF16 field against the FP64 kernels
 
 Prints one JSON line on rank 0.
 """
@@ -419,6 +420,60 @@ def run_study(args):
     return 0
 
 
+def run_precision(args):
+    """Storage forms of the full-size passive registration (NEXT-1): images as
+    float or int16 HU, field as FP32 or BF16, arithmetic FP32, reductions FP64.
+    Error against the FP64 form of the same kernels (precision = DIR_F64, which
+    matches the FP64 oracle to 1e-9 voxel on this workload), landmark error,
+    algorithmic bytes per voxel-update and time.  Schedules: single scale, 50
+    iterations (the 64^3-style parity schedule on the full-size inputs), and the
+    3-level 200/100/50 pyramid."""
+    import numpy as np
+    import torch
+    import paper_0909_0928_gb300 as dl
+    from phantom import FULL, make_lung_phantom
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    ph = make_lung_phantom(FULL)
+    S16 = np.round(ph["S"]).astype(np.int16)
+    M16 = np.round(ph["M"]).astype(np.int16)
+    imgs = {"f32": (torch.from_numpy(S16.astype(np.float32)).cuda(),
+                    torch.from_numpy(M16.astype(np.float32)).cuda(), dl.DIR_F32),
+            "i16": (torch.from_numpy(S16).cuda(), torch.from_numpy(M16).cuda(), dl.DIR_I16)}
+    lm, ut = ph["landmarks"], ph["u_true_mm"]
+    # bytes per voxel-update of the finest-level two-kernel iteration
+    bpv = {("f32", "f32"): 56, ("i16", "f32"): 52, ("f32", "bf16"): 32, ("i16", "bf16"): 28}
+    out = {"mode": "precision", "workload": "256x256x100 lung phantom rounded to int16 HU, passive"}
+    for sched_name, levels, iters in (("single_scale_50", 1, [50]), ("pyramid_200_100_50", 3, ITERS)):
+        def run(img, field, precision=dl.DIR_F32):
+            S_d, M_d, dt = imgs[img]
+            p = dl.dir_params_default(levels=levels, iters=iters, precision=precision,
+                                      field_dtype=dl.DIR_BF16 if field == "bf16" else dl.DIR_F32)
+            ctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dt, True, 0, p, stream)
+            try:
+                dl.dir_register(ctx)
+                ms = statistics.median([dl.dir_register(ctx).ms_total for _ in range(5)])
+                u = np.empty((3,) + ph["S"].shape, np.float64)
+                dl.dir_get_field_f64(ctx, u)
+            finally:
+                dl.dir_destroy(ctx)
+            return u, ms
+        ref, ms64 = run("f32", "f32", dl.DIR_F64)
+        res = {"reference": {"precision": "f64 kernels", "ms": ms64}}
+        for img, field in (("f32", "f32"), ("i16", "f32"), ("f32", "bf16"), ("i16", "bf16")):
+            u, ms = run(img, field)
+            err = np.abs(u - ref).max(axis=0)
+            m, sd = landmark_error_mm(u.astype(np.float32), lm, ut, SPACING)
+            res[f"images_{img}_field_{field}"] = {
+                "ms": ms, "bytes_per_voxel_update_finest": bpv[(img, field)],
+                "max_du_vs_f64": float(err.max()), "q99_du_vs_f64": float(np.quantile(err, 0.99)),
+                "median_du_vs_f64": float(np.median(err)),
+                "landmark_mm": {"mean": m, "sd": sd}}
+        out[sched_name] = res
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,7 +484,7 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch", "study"])
+    ap.add_argument("--form", default="plain", choices=["plain", "batch", "study", "precision"])
     ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2],
                     help="fold the Gaussian into the next force pass (Eqs. 1-2): 0 never, "
                          "1 every level, 2 (library default) the small levels")
@@ -443,6 +498,8 @@ def main():
         return run_batch(args)
     if args.form == "study":
         return run_study(args)
+    if args.form == "precision":
+        return run_precision(args)
 
     import numpy as np
     import torch
