@@ -215,7 +215,7 @@ struct FGGeom {
     static constexpr int SBOX = UD * FSH * FSW * (int)sizeof(TI);  // [UD][FSH][FSW]
     static constexpr int HX = FTX + 2, HY = FTY + 2, HZ = FTZ + 2;
     static constexpr int WT = HZ * HY * HX * 4;                    // D on brick + halo
-    static constexpr int DT = IC ? FTZ * FTY * FTX * 4 : 0;        // Eq. 6: d on the brick
+    static constexpr int DT = 0;                                   // d stays in registers
     static constexpr int OFF_S = (UBOX + 127) / 128 * 128;
     static constexpr int OFF_W = OFF_S + (SBOX + 127) / 128 * 128;
     static constexpr int OFF_D = OFF_W + (WT + 127) / 128 * 128;
@@ -238,7 +238,6 @@ __global__ void __launch_bounds__(FNT, 4)
     const float* ub = reinterpret_cast<const float*>(base);       // [3][UD][UH][UW]
     const TI* sb = reinterpret_cast<const TI*>(base + F::OFF_S);  // [UD][FSH][FSW]
     float* wt = reinterpret_cast<float*>(base + F::OFF_W);        // [HZ][HY][HX]
-    float* dt = reinterpret_cast<float*>(base + F::OFF_D);        // [FTZ][FTY][FTX] (Eq. 6)
     uint64_t* bar = reinterpret_cast<uint64_t*>(base + F::OFF_BAR);
     const Grid3 g = a.g;
     const TI* __restrict__ S = static_cast<const TI*>(a.S);
@@ -280,32 +279,61 @@ __global__ void __launch_bounds__(FNT, 4)
     const Interp ip(g);
     constexpr int UC = UD * UH * UW;  // floats per u component in the box
 
-    // D on the brick plus a one-voxel halo (clamped positions; all inside the boxes)
-    for (int q = tid; q < HX * HY * HZ; q += FNT) {
-        const int hz = q / (HX * HY);
-        const int r = q - hz * (HX * HY);
-        const int hy = r / HX, hx = r - hy * HX;
-        const int gx = clampi(bx0 + hx - 1, 0, g.nx - 1);
-        const int gy = clampi(by0 + hy - 1, 0, g.ny - 1);
-        const int gz = clampi(bz0 + hz - 1, 0, g.nz - 1);
+    // D (= W - S) at one clamped position of the brick + halo footprint; all
+    // reads from the boxes (every clamped position lies inside them)
+    auto d_at = [&](int gx, int gy, int gz, float& dd) -> float {
         const int ui = ((gz - uz0) * UH + (gy - uy0)) * UW + (gx - ux0);
         const float ux = ub[ui], uy = ub[ui + UC], uz = ub[ui + 2 * UC];
         const float sref = (float)sb[((gz - sz0) * FSH + (gy - sy0)) * FSW + (gx - sx0)];
         const float wm = interp_rel(M, ip, gx, ux, gy, uy, gz, uz, sref);
         if (F::IC) {
             const float ws = interp_rel(S, ip, gx, -ux, gy, -uy, gz, -uz, sref);
-            wt[q] = wm + ws;
-            if (hx >= 1 && hx <= FTX && hy >= 1 && hy <= FTY && hz >= 1 && hz <= FTZ)
-                dt[((hz - 1) * FTY + (hy - 1)) * FTX + (hx - 1)] = wm - ws;
-        } else {
-            wt[q] = wm;
+            dd = wm - ws;
+            return wm + ws;
         }
-    }
-    __syncthreads();
-
+        dd = wm;
+        return wm;
+    };
     const int x = bx0 + tx, y = by0 + ty;
     const bool col_valid = (x < g.nx) && (y < g.ny);
     const int xc = min(x, g.nx - 1), yc = min(y, g.ny - 1);
+    // this thread's own column, planes bz0-1 .. bz0+FTZ: D kept in registers
+    // (for the z gradient and d) and written to the tile for the neighbours
+    float dcol[FTZ + 2];  // D (Eq. 6: D_m + D_s)
+    float dd[FTZ];        // d at the brick's planes (Eq. 6: D_m - D_s)
+#pragma unroll
+    for (int h = 0; h < FTZ + 2; ++h) {
+        float t;
+        dcol[h] = d_at(xc, yc, clampi(bz0 + h - 1, 0, g.nz - 1), t);
+        if (h >= 1 && h <= FTZ) dd[h - 1] = t;
+        wt[(h * HY + (ty + 1)) * HX + (tx + 1)] = dcol[h];
+    }
+    // the 2 (HX + HY) - 4 = 84 border columns of the footprint, FTZ + 2 planes
+    // each, spread over all threads
+    constexpr int NB = 2 * (HX + HY) - 4;
+    for (int q = tid; q < NB * HZ; q += FNT) {
+        const int hz = q / NB, b = q - hz * NB;
+        int hx, hy;
+        if (b < HX) {
+            hx = b;
+            hy = 0;
+        } else if (b < 2 * HX) {
+            hx = b - HX;
+            hy = HY - 1;
+        } else if (b < 2 * HX + (HY - 2)) {
+            hx = 0;
+            hy = 1 + (b - 2 * HX);
+        } else {
+            hx = HX - 1;
+            hy = 1 + (b - 2 * HX - (HY - 2));
+        }
+        float t;
+        wt[(hz * HY + hy) * HX + hx] =
+            d_at(clampi(bx0 + hx - 1, 0, g.nx - 1), clampi(by0 + hy - 1, 0, g.ny - 1),
+                 clampi(bz0 + hz - 1, 0, g.nz - 1), t);
+    }
+    __syncthreads();
+
     const int sx = xc - sx0, sxm = max(xc - 1, 0) - sx0, sxp = min(xc + 1, g.nx - 1) - sx0;
     const int sy = yc - sy0, sym = max(yc - 1, 0) - sy0, syp = min(yc + 1, g.ny - 1) - sy0;
     const int cs = (int)g.cs;
@@ -322,14 +350,15 @@ __global__ void __launch_bounds__(FNT, 4)
                 const float gsy = 0.5f * ((float)Sc[syp * FSW + sx] - (float)Sc[sym * FSW + sx]);
                 const float gsz = 0.5f * ((float)sb[pp * (FSH * FSW) + sy * FSW + sx] -
                                           (float)sb[pm * (FSH * FSW) + sy * FSW + sx]);
-                // grad W = grad D + grad S (Eq. 6: grad(D_m + D_s) + 2 grad S), with
-                // the tile's clamped neighbours as in force_kernel
+                // grad W = grad D + grad S (Eq. 6: grad(D_m + D_s) + 2 grad S); the
+                // footprint's clamped positions make the neighbours of an edge
+                // voxel the clamped ones, as in force_kernel
                 const float ns = F::IC ? 2.0f : 1.0f;
                 const float* W1 = wt + ((k + 1) * HY + (ty + 1)) * HX + (tx + 1);
                 const float gmx = r_fma(ns, gsx, 0.5f * (W1[1] - W1[-1]));
                 const float gmy = r_fma(ns, gsy, 0.5f * (W1[HX] - W1[-HX]));
-                const float gmz = r_fma(ns, gsz, 0.5f * (W1[HX * HY] - W1[-HX * HY]));
-                const float d = F::IC ? dt[(k * FTY + ty) * FTX + tx] : W1[0];
+                const float gmz = r_fma(ns, gsz, 0.5f * (dcol[k + 2] - dcol[k]));
+                const float d = dd[k];
                 const int ui = (((k + 1) * UH) + (ty + 1)) * UW + (tx + 4);
                 const float ux = ub[ui], uy = ub[ui + UC], uz = ub[ui + 2 * UC];
                 float dx, dy, dz;
