@@ -412,6 +412,39 @@ def make_blob_pair(dims, shift_vox, seed: int = 7, n_blobs: int = 12,
     return S.astype(np.float32), M.astype(np.float32)
 
 
+def make_wave_pair(dims, shift_vox, seed: int = 9, n_terms: int = 3,
+                   wavelength_vox: tuple = (20.0, 60.0),
+                   amplitude: float = 100.0) -> tuple[np.ndarray, np.ndarray]:
+    """S = sum of separable products of cosines; M(y) = S(y - T).
+
+    Each term is a * cos(2 pi x / lx + px) cos(2 pi y / ly + py) cos(2 pi z / lz + pz)
+    with seeded wavelengths in `wavelength_vox` and phases, so a volume of any
+    size is built from 1-D factors (outer products) in a second or two.  As for
+    make_blob_pair, the field that registers the pair is u = T.  Returns
+    float32 (S, M) of shape (nz, ny, nx).
+    """
+    nx, ny, nz = dims
+    rng = SplitMix64Stream(seed, sid=7)
+    lam = rng.uniform(3 * n_terms, wavelength_vox[0], wavelength_vox[1]).reshape(n_terms, 3)
+    phase = rng.uniform(3 * n_terms, 0.0, 2.0 * math.pi).reshape(n_terms, 3)
+    amp = amplitude * rng.uniform(n_terms, 0.5, 1.0)
+    axes = [np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64),
+            np.arange(nz, dtype=np.float64)]
+    t = np.asarray(shift_vox, dtype=np.float64)
+
+    def volume(off):
+        acc = np.zeros((nz, ny, nx))
+        for k in range(n_terms):
+            f = [np.cos(2.0 * math.pi * (axes[a] - off[a]) / lam[k, a] + phase[k, a])
+                 for a in range(3)]
+            acc += amp[k] * f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :]
+        return acc
+
+    S = volume(np.zeros(3))
+    M = volume(t)
+    return S.astype(np.float32), M.astype(np.float32)
+
+
 def random_volume(dims, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """Uniform random float64 volume of shape (nz, ny, nx), for unit tests."""
     nx, ny, nz = dims

@@ -406,3 +406,62 @@ def test_full_size_parity(dl, full_phantom, variant, alpha):
     err = np.linalg.norm(ue - full_phantom["u_true_mm"], axis=1)
     init = np.linalg.norm(full_phantom["u_true_mm"], axis=1)
     assert err.mean() < 0.5 * init.mean()
+
+
+# ------------------------------------------------------------ maximum size
+
+MAX_DIMS = (512, 512, 160)   # the largest volume of the serving mix
+
+
+@pytest.fixture(scope="module")
+def wave_max():
+    from phantom import make_wave_pair
+    return make_wave_pair(MAX_DIMS, (1.5, -0.75, 0.5), seed=21)
+
+
+def _crop_origins(dims, size, n_interior, seed):
+    """Origins (x, y, z) of cubes of side `size`: the two opposite corners of
+    the volume and `n_interior` seeded ones."""
+    from phantom import SplitMix64Stream
+    n = np.array(dims)
+    out = [(0, 0, 0), tuple(int(v) for v in n - size)]
+    r = SplitMix64Stream(seed, sid=3).uniform(3 * n_interior).reshape(n_interior, 3)
+    for row in r:
+        out.append(tuple(int(v) for v in (size + row * (n - 3 * size)).astype(int)))
+    return out
+
+
+@pytest.mark.parametrize("variant", [0, 2, 5])
+def test_max_size_sampled_parity(dl, wave_max, variant):
+    # 512 x 512 x 160 (int32 offsets across three field components, the
+    # largest grids), one level, two iterations.  Each output voxel then
+    # depends on a neighbourhood of radius below 12 (two smoothings of radius
+    # 3, gradients of radius 1, gathers and the Eq. 6 inversion within a voxel
+    # or two), so the oracle on a 48^3 crop gives the exact result on the
+    # voxels at least 12 from every crop face that is not a face of the volume.
+    import oracle
+    S, M = wave_max
+    g = gpu_register(dl, S, M, variant, 1, [2])
+    C, m = 48, 12
+    worst = 0.0
+    for x0, y0, z0 in _crop_origins(MAX_DIMS, C, 3, seed=5 + variant):
+        sl = (slice(z0, z0 + C), slice(y0, y0 + C), slice(x0, x0 + C))
+        ref = oracle.register(np.ascontiguousarray(S[sl]), np.ascontiguousarray(M[sl]),
+                              variant=variant, levels=1, iters=(2,))["u"]
+        core = []
+        for o, n in ((z0, MAX_DIMS[2]), (y0, MAX_DIMS[1]), (x0, MAX_DIMS[0])):
+            core.append(slice(0 if o == 0 else m, C if o + C == n else C - m))
+        core = tuple(core)
+        got = g["u"][(slice(None),) + sl].astype(np.float64)
+        err = float(np.abs(got[(slice(None),) + core] - ref[(slice(None),) + core]).max())
+        worst = max(worst, err)
+        assert err <= TOL_U, f"crop at {(x0, y0, z0)}: max|du| {err:.3e}"
+    print(f"max size v{variant}: max|du| {worst:.2e} on the crop cores")
+
+
+def test_max_size_equal_images_give_zero_field(dl, wave_max):
+    # the default schedule (3 levels, 200/100/50, fused small levels) at the
+    # largest size: equal images leave every field component exactly zero
+    S, _ = wave_max
+    g = gpu_register(dl, S, S, 0, 3, [200, 100, 50], fuse=2)
+    assert not np.any(g["u"])

@@ -1,7 +1,7 @@
 """The seeded input generator: determinism, shapes and the true deformation."""
 import numpy as np
 
-from phantom import SMALL, SplitMix64Stream, make_lung_phantom, true_field_mm
+from phantom import SMALL, SplitMix64Stream, make_lung_phantom, make_wave_pair, true_field_mm
 from phantom.generator import _build_geometry, backward_map_mm
 
 
@@ -47,3 +47,14 @@ def test_true_field_solves_the_backward_map(small_phantom):
     assert np.abs(resid).max() < 1e-8
     mag = np.linalg.norm(u, axis=1)
     assert 1.0 < mag.mean() < SMALL.a_max_mm + 5.0
+
+
+def test_wave_pair_is_a_pure_shift():
+    # M(y) = S(y - T): for an integer T the moving volume is the static one
+    # moved by T voxels, value for value
+    S, M = make_wave_pair((40, 30, 20), (2, 3, 1), seed=4)
+    assert S.shape == (20, 30, 40) and S.dtype == np.float32
+    assert np.array_equal(M[1:, 3:, 2:], S[:-1, :-3, :-2])
+    S2, M2 = make_wave_pair((40, 30, 20), (2, 3, 1), seed=4)
+    assert np.array_equal(S, S2) and np.array_equal(M, M2)
+    assert not np.array_equal(S, make_wave_pair((40, 30, 20), (2, 3, 1), seed=5)[0])
