@@ -379,7 +379,7 @@ def test_conditioning_of_the_iteration(small_phantom):
     # perturbing every input voxel by one FP32 ulp (relative 2^-23) moves the
     # FP64 passive result by far less than the 1e-3 voxel parity bar, but the
     # double force (steps up to 1 voxel, Eq. 4) by more than the bar, on the
-    # clamped boundary planes.  FP32 parity is therefore judged on conditioned
+    # clamped boundary planes.  FP32 parity is therefore assessed on conditioned
     # voxels only, and the FP64 build of the kernels is compared everywhere.
     from phantom import SplitMix64Stream
     p = small_phantom
