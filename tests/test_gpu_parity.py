@@ -227,6 +227,24 @@ def test_equal_images_give_zero_field(dl, small_phantom):
         assert np.array_equal(g["u"], np.zeros_like(g["u"])), v
 
 
+@pytest.mark.parametrize("variant", [0, 5])
+def test_levels_without_iterations(dl, variant):
+    # zero iterations everywhere leave the field at zero (Eq. 6: the inverted
+    # mid-space field of h = 0); a level with none in the middle of the
+    # schedule only up-samples the field on to the next level
+    import oracle
+    from phantom import make_blob_pair
+    S, M = make_blob_pair((40, 36, 24), (1.0, -0.5, 0.5), seed=3, n_blobs=12, sigma_vox=4.0)
+    g = gpu_register(dl, S, M, variant, 3, [0, 0, 0], fuse=2)
+    assert not np.any(g["u"]) and g["hist"].shape[0] == 0
+    ref = oracle.register(S, M, variant=variant, levels=3, iters=(3, 0, 2))
+    g64 = gpu_register(dl, S, M, variant, 3, [3, 0, 2], fp64=True)
+    check64(g64, ref, f"iters 3/0/2 v{variant}")
+    g = gpu_register(dl, S, M, variant, 3, [3, 0, 2], fuse=2)
+    err = float(np.abs(g["u"].astype(np.float64) - ref["u"]).max())
+    assert err <= TOL_U, err
+
+
 def test_graph_replay_matches_direct_launch_and_is_deterministic(dl, small_phantom):
     S, M = small_phantom["S"], small_phantom["M"]
     a = gpu_register(dl, S, M, 2, 2, [10, 10], use_graph=1, repeat=3)
