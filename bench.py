@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -109,10 +110,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and blank lines: a change of comments
+    alone leaves a kernel, and so its recorded ncu counters, as they were."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def sources_sha256(kernel: str) -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(ROOT, "paper_0909_0928_gb300", "csrc", f), "rb").read())
+        path = os.path.join(ROOT, "paper_0909_0928_gb300", "csrc", f)
+        h.update(_code_only(open(path, encoding="utf-8").read()).encode())
     return h.hexdigest()
 
 

@@ -1,12 +1,17 @@
 // dir_smooth.cu -- separable 3-D Gaussian low-pass filter (Sec. 2.5).
 //
 // out = G_sigma * in, applied along x, then y, then z, with replicated edges,
-// on 1 or 3 components: the TMA-fed plane pipeline of dir_stencil.cuh.  A
-// block smooths one component of a 32 x 8 column tile over a z chunk, one
-// thread per (column, 4-row group) for the y and z passes, so the three
-// components run as independent blocks (three times the marching chains per
-// SM).  Every input voxel is read from HBM about once per launch (plus the
-// 2R-plane halo of each z chunk).
+// on 1 or 3 components, in three forms:
+//  * smooth2_kernel (single-precision fields): one component of a 32 x TY
+//    tile (TY = 32 on large levels, 16 otherwise) over a z chunk, fed by a
+//    ring of TMA plane copies, y and z passes on packed f32x2 row pairs;
+//  * smooth_small_kernel (single precision, small levels): all planes of a
+//    two-plane chunk and all three components in one TMA copy;
+//  * smooth_kernel (double precision, int16 or bf16 storage): the TMA-fed
+//    plane pipeline of dir_stencil.cuh on 32 x 8 tiles.
+// The components run as independent blocks (three times the marching chains
+// per SM).  Every input voxel is read from HBM about once per launch (plus
+// the 2R-plane halo of each z chunk).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -70,8 +75,8 @@ __global__ void __launch_bounds__(StencilGeom<Real, R, 1, 8, TIN>::YT)
 
 // ---------------------------------------------------------------------------
 // Single-precision field smoothing, packed (building blocks and layout in
-// dir_smooth2.cuh): a block of 128 threads smooths one component of a
-// 32 x 16 tile over a z chunk, fed by a 6-deep ring of TMA plane copies.
+// dir_smooth2.cuh): a block of 8 TY threads smooths one component of a
+// 32 x TY tile over a z chunk, fed by a 6-deep ring of TMA plane copies.
 // ---------------------------------------------------------------------------
 constexpr int S2STAGES = 6;
 constexpr bool kSmoothTall = true;  // 32-row tiles on large levels
