@@ -248,6 +248,22 @@ int dir_register_noalloc(const float* static_img, const float* moving_img, const
                          dir_variant variant, const dir_params* params, float* field_out,
                          void* cuda_stream, dir_stats* stats_out);
 
+/*
+ * Exercises the failure path of the bounded device-side waits that every
+ * TMA-fed kernel of the library uses (a kernel whose copy never lands gives
+ * up, flags the context's error word and returns; the call then reports
+ * DIR_ETIMEOUT).  One block waits on a shared-memory mbarrier that nothing
+ * completes -- no copy is involved and nothing faults -- for limit_ms, gives
+ * up, and records that in a device word that the call reads back.
+ *   cuda_stream  a cudaStream_t, or NULL for the legacy default stream
+ *   limit_ms     how long the wait lasts before it gives up, 1 .. 2000
+ * Returns DIR_ETIMEOUT when the wait gave up as designed (the expected
+ * outcome; the device stays usable), DIR_EINVAL for a limit out of range,
+ * DIR_ECUDA on a CUDA error, DIR_OK if the wait were ever satisfied.
+ * Waits for the stream.
+ */
+int dir_check_wait_timeout(void* cuda_stream, double limit_ms);
+
 /* Frees ctx and everything it owns.  NULL-safe. */
 void dir_destroy(dir_ctx* ctx);
 

@@ -8,7 +8,9 @@ importing this package raises.
 
 Functions carry the C names: dir_params_default, dir_create, dir_load,
 dir_register, dir_register_async, dir_sync, dir_get_field, dir_get_field_f64,
-dir_get_history, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version.
+dir_get_history, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version,
+dir_register_noalloc, dir_batch_create, dir_batch_run, dir_batch_destroy,
+dir_autotune, dir_check_wait_timeout.
 `Registration` wraps a context for convenience.
 """
 from __future__ import annotations
@@ -34,7 +36,8 @@ VARIANTS = {"passive": 0, "evolved_passive": 1, "active": 2, "double": 3, "adjus
 EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_register_async",
            "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history", "dir_warp", "dir_destroy",
            "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc",
-           "dir_batch_create", "dir_batch_run", "dir_batch_destroy", "dir_autotune"]
+           "dir_batch_create", "dir_batch_run", "dir_batch_destroy", "dir_autotune",
+           "dir_check_wait_timeout"]
 
 
 class DirParams(C.Structure):
@@ -99,6 +102,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_batch_run": (ip, [vp, C.POINTER(C.c_float)]),
         "dir_batch_destroy": (None, [vp]),
         "dir_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
+        "dir_check_wait_timeout": (ip, [vp, C.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +262,13 @@ def dir_register_noalloc(static_img, moving_img, dims, variant=DIR_PASSIVE,
 def dir_destroy(ctx):
     if ctx is not None:
         _lib.dir_destroy(ctx)
+
+
+def dir_check_wait_timeout(stream=None, limit_ms: float = 100.0) -> int:
+    """Runs the library's bounded device-side wait on a barrier that nothing
+    completes and returns the status code (DIR_ETIMEOUT when the wait gave up
+    as designed)."""
+    return int(_lib.dir_check_wait_timeout(_stream_handle(stream), float(limit_ms)))
 
 
 def dir_batch_create(ctxs, branches: int = 8, stream=None):

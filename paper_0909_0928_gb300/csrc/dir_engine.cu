@@ -848,6 +848,24 @@ const char* dir_last_error(const dir_ctx* c) { return c ? c->err.c_str() : g_cre
 
 const char* dir_version(void) { return "gb300-demons 0.2 (sm_103a)"; }
 
+int dir_check_wait_timeout(void* stream_ptr, double limit_ms) {
+    if (!(limit_ms >= 1.0 && limit_ms <= 2000.0)) return DIR_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream_ptr);
+    int* word = nullptr;
+    int flagged = 0;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&word), sizeof(int), s) != cudaSuccess)
+        return DIR_ECUDA;
+    bool ok = cudaMemsetAsync(word, 0, sizeof(int), s) == cudaSuccess &&
+              dirk::launch_wait_probe(word, (unsigned long long)(limit_ms * 1.0e6), s) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(&flagged, word, sizeof(int), cudaMemcpyDeviceToHost, s) ==
+                  cudaSuccess;
+    ok = cudaFreeAsync(word, s) == cudaSuccess && ok;
+    ok = cudaStreamSynchronize(s) == cudaSuccess && ok;
+    if (!ok) return DIR_ECUDA;
+    return (flagged & dirk::kErrTmaTimeout) ? DIR_ETIMEOUT : DIR_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------

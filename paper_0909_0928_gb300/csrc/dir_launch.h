@@ -94,6 +94,9 @@ cudaError_t launch_export_field(bool fp64, int ftype, const void* field, const G
 // pitched[c] = dense float input converted to out_type, for ncomp components
 cudaError_t launch_import(bool fp64, int out_type, const float* dense, void* pitched,
                           const Grid3& g, int ncomp, cudaStream_t s);
+// one bounded wait on an mbarrier that never completes; sets kErrTmaTimeout
+// in *err when it gives up after limit_ns
+cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_t s);
 // relative-norm stop test of Sec. 2.4 for iteration t of a level
 cudaError_t launch_stop_test(const double* red, double* lhist, int t, int level_first, int window,
                              double eps, int* stop_iter, int iter_in_level, cudaStream_t s);

@@ -199,6 +199,21 @@ cudaError_t launch_import(bool fp64, int out_type, const float* dense, void* pit
     return cudaGetLastError();
 }
 
+// One thread waits, bounded, on an mbarrier that nothing arrives on (the
+// failure path of the TMA waits), then records that it gave up.
+__global__ void wait_probe_kernel(int* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, kErrTmaTimeout);
+}
+
+cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_t s) {
+    wait_probe_kernel<<<1, 32, 0, s>>>(err, limit_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stop_test(const double* red, double* lhist, int t, int level_first, int window,
                              double eps, int* stop_iter, int iter_in_level, cudaStream_t s) {
     stop_test_kernel<<<1, 1, 0, s>>>(red, lhist, t, level_first, window, eps, stop_iter,

@@ -483,3 +483,23 @@ def test_max_size_equal_images_give_zero_field(dl, wave_max):
     S, _ = wave_max
     g = gpu_register(dl, S, S, 0, 3, [200, 100, 50], fuse=2)
     assert not np.any(g["u"])
+
+
+# ------------------------------------------------------------ failure path
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable(dl, small_phantom):
+    # the wait that every TMA-fed kernel bounds, run on a barrier that nothing
+    # completes: it gives up after the limit, the call reports DIR_ETIMEOUT,
+    # and the next registration runs as before
+    import time
+    S, M = small_phantom["S"], small_phantom["M"]
+    before = gpu_register(dl, S, M, 0, 2, [5, 5])
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    rc = dl.dir_check_wait_timeout(stream, 100.0)
+    dt = time.perf_counter() - t0
+    assert rc == dl.DIR_ETIMEOUT, rc
+    assert 0.09 <= dt < 5.0, dt
+    assert dl.dir_check_wait_timeout(stream, 0.0) == dl.DIR_EINVAL
+    after = gpu_register(dl, S, M, 0, 2, [5, 5])
+    assert np.array_equal(before["u"], after["u"])
