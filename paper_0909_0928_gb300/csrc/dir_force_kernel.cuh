@@ -103,8 +103,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 
 // Prefetch into L2 the rows of the brick that block `b` (linear block index)
 // will read: u (three components) over its FTZ planes, S and M over the planes
-// one below to one above.  Issued for the block one wave ahead, so that its
-// loads of u and S (and M near its voxels) hit L2 instead of HBM.
+// one below to one above.  Issued for the block pf_stride positions ahead, so
+// that its loads of u and S (and M near its voxels) hit L2 instead of HBM.
 template <int FTZ, typename TI, typename TF>
 __device__ __forceinline__ void prefetch_brick(const ForceArgs& a, long long b, int tid, int nt) {
     const Grid3& g = a.g;

@@ -8,8 +8,9 @@
 // one-voxel halo (and of M, for Eq. 2's |grad M|) with one bulk tensor copy
 // each, waits once, and then reads them from shared memory; only the gathers
 // of M at x + u go through L1/L2.  Thread 0 also asks L2 to prefetch the
-// bricks of the block one wave ahead (cp.async.bulk.prefetch.tensor), so that
-// later waves find their operands in L2.
+// bricks of the block pf_stride positions ahead (one block per SM ahead by
+// default; cp.async.bulk.prefetch.tensor), so that later blocks find their
+// operands in L2.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(FNT, 4)
         tma_load_4d(base, &umap, bx0, by0, bz0, 0, bar);
         tma_load_4d(base + F::OFF_S, &smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
         if (V == 1) tma_load_4d(base + F::OFF_M, &mmap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
-        // the block one wave ahead: its bricks into L2
+        // the block pf_stride positions ahead: its bricks into L2
         if (a.pf_stride > 0) {
             const long long gx = gridDim.x, gy = gridDim.y;
             const long long b = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) +
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(FNT, 4)
         mbar_arrive_expect_tx(bar, (uint32_t)(F::UBOX + F::SBOX));
         tma_load_4d(base, &umap, ux0, uy0, uz0, 0, bar);
         tma_load_4d(base + F::OFF_S, &smap, sx0, sy0, sz0, 0, bar);
-        if (a.pf_stride > 0) {  // the block one wave ahead: its boxes into L2
+        if (a.pf_stride > 0) {  // the block pf_stride positions ahead: its boxes into L2
             const long long gx = gridDim.x, gy = gridDim.y;
             const long long b = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) +
                                 a.pf_stride;

@@ -30,7 +30,7 @@ struct ForceArgs {
     int img_type;        // storage of S and M at this level (kStore*)
     int field_type;      // storage of u and v (kStore*)
     int pf_stride = 0;   // > 0: each block prefetches into L2 the brick of the block
-                         // this many linear indices ahead (about one wave)
+                         // this many linear indices ahead
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
 };
 cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
