@@ -1083,6 +1083,7 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         fa.img_type = c->img_type(l);
         fa.field_type = c->field_type;
         fa.err = c->derr;
+        fa.pf_stride = c->num_sms;  // as in the registration
         float best = 1e30f;
         int best_d = 0;
         for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {
