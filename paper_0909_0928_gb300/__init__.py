@@ -136,6 +136,22 @@ def _ptr(x, want_device: bool):
     return C.c_void_p(a.ctypes.data)
 
 
+_ITEMSIZE = {DIR_F32: 4, DIR_I16: 2, DIR_F16: 2, DIR_BF16: 2, DIR_F64: 8}
+
+
+def _check_buffer(x, count: int, itemsize: int, name: str):
+    """The library reads or writes exactly `count` elements of `itemsize`
+    bytes through the pointer: refuse anything smaller or of another width."""
+    if _is_torch(x):
+        n, w = int(x.numel()), int(x.element_size())
+    else:
+        a = np.asarray(x)
+        n, w = int(a.size), int(a.itemsize)
+    if n != count or w != itemsize:
+        raise ValueError(f"{name}: expected {count} elements of {itemsize} bytes, "
+                         f"got {n} of {w}")
+
+
 def _stream_handle(stream) -> C.c_void_p:
     if stream is None:
         return C.c_void_p(0)
@@ -188,6 +204,10 @@ def dir_create(static_img, moving_img, dims, spacing_mm=(1.0, 1.0, 1.0), image_d
     out = C.c_void_p()
     d = (C.c_int * 3)(*[int(x) for x in dims])
     s = (C.c_float * 3)(*[float(x) for x in spacing_mm])
+    n = d[0] * d[1] * d[2]
+    if n > 0 and int(image_dtype) in (DIR_F32, DIR_I16):  # the image storage types
+        _check_buffer(static_img, n, _ITEMSIZE[int(image_dtype)], "static_img")
+        _check_buffer(moving_img, n, _ITEMSIZE[int(image_dtype)], "moving_img")
     rc = _lib.dir_create(C.byref(out), _ptr(static_img, inputs_on_device),
                          _ptr(moving_img, inputs_on_device), C.byref(d), C.byref(s),
                          int(image_dtype), int(bool(inputs_on_device)), int(variant),
@@ -328,6 +348,7 @@ class Registration:
             out = np.empty((3, nz, ny, nx), dtype=np.float64 if f64 else np.float32)
         on_dev = _is_torch(out) and bool(out.is_cuda)
         is64 = (str(out.dtype).endswith("float64"))
+        _check_buffer(out, 3 * nx * ny * nz, 8 if is64 else 4, "field out")
         (dir_get_field_f64 if is64 else dir_get_field)(self.ctx, out, in_mm, on_dev)
         return out
 
@@ -338,6 +359,9 @@ class Registration:
         on_dev = _is_torch(img) and bool(img.is_cuda)
         if out is None:
             out = np.empty_like(img) if not on_dev else img.new_empty(img.shape)
+        nx, ny, nz = self.dims
+        _check_buffer(img, nx * ny * nz, 4, "warp input")
+        _check_buffer(out, nx * ny * nz, 4, "warp output")
         dir_warp(self.ctx, img, out, DIR_F32, on_dev)
         return out
 

@@ -90,3 +90,17 @@ def test_argument_checks_precede_device_work(dl):
 
 def test_null_safe_destroy(dl):
     dl._lib.dir_destroy(None)
+
+
+def test_binding_refuses_buffers_of_the_wrong_size_or_width(dl):
+    # the C calls take plain pointers; the binding checks what it can before
+    # handing one over
+    S = np.zeros((4, 4, 4), np.float32)
+    with pytest.raises(ValueError):
+        dl.dir_create(S, S[:3], (4, 4, 4), (1, 1, 1))
+    with pytest.raises(ValueError):
+        dl.dir_create(S.astype(np.float64), S.astype(np.float64), (4, 4, 4), (1, 1, 1))
+    with pytest.raises(ValueError):
+        dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), image_dtype=dl.DIR_I16)
+    with pytest.raises(ValueError):
+        dl.dir_create(S, S, (4, 4, 5), (1, 1, 1))
