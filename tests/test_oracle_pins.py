@@ -423,3 +423,29 @@ def test_single_precision_state_probe(small_phantom):
     b = oracle.register(S, M, variant=3, levels=1, iters=[50], probe_rel=1.0,
                         probe_seed=oracle.ROUND32)["u"]
     assert np.abs(a - b).max() > 1e-3
+
+
+@pytest.mark.parametrize("variant", [0, 2, 5])
+def test_two_iterations_are_local(variant):
+    # the largest-size GPU parity test relies on this: after one level of two
+    # iterations each output voxel depends only on a neighbourhood of radius
+    # below 12, so a crop of the inputs reproduces the whole-volume result on
+    # the voxels at least 12 from every crop face inside the volume
+    from phantom import make_wave_pair
+    dims = (80, 72, 60)
+    S, M = make_wave_pair(dims, (1.5, -0.75, 0.5), seed=21)
+    full = oracle.register(S, M, variant=variant, levels=1, iters=(2,))["u"]
+    C, m = 40, 12
+    for x0, y0, z0 in [(0, 0, 0), (dims[0] - C, dims[1] - C, dims[2] - C), (20, 17, 11)]:
+        sl = (slice(z0, z0 + C), slice(y0, y0 + C), slice(x0, x0 + C))
+        crop = oracle.register(np.ascontiguousarray(S[sl]), np.ascontiguousarray(M[sl]),
+                               variant=variant, levels=1, iters=(2,))["u"]
+        core = tuple(slice(0 if o == 0 else m, C if o + C == n else C - m)
+                     for o, n in ((z0, dims[2]), (y0, dims[1]), (x0, dims[0])))
+        a = full[(slice(None),) + sl][(slice(None),) + core]
+        b = crop[(slice(None),) + core]
+        assert np.abs(a - b).max() <= 1e-12
+        assert np.abs(a).max() > 0.1  # the field has moved
+    # and the margin matters: two voxels from an inner face the crop differs
+    near = (slice(None),) + (slice(2, C - 2),) * 3
+    assert np.abs(full[(slice(None),) + sl][near] - crop[near]).max() > 1e-3
