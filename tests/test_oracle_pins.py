@@ -274,6 +274,42 @@ def test_equal_images_give_zero_update_all_variants():
         assert red[0] == 0.0 and red[1] == 0.0 and red[2] == 0.0
 
 
+def _brute_gauss(vol, sigma):
+    """Non-separable (2R+1)^3 convolution with replicated edges, taps written
+    out from the closed form exp(-t^2 / 2 sigma^2) / sum."""
+    R = math.ceil(3 * sigma)
+    t = np.arange(-R, R + 1, dtype=float)
+    w = np.exp(-t * t / (2 * sigma * sigma))
+    w /= w.sum()
+    nz, ny, nx = vol.shape
+    P = np.pad(vol, R, mode="edge")
+    out = np.zeros_like(vol)
+    for a in range(2 * R + 1):
+        for b in range(2 * R + 1):
+            for c in range(2 * R + 1):
+                out += w[a] * w[b] * w[c] * P[a:a + nz, b:b + ny, c:c + nx]
+    return out
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_iteration_smooths_the_total_field(variant):
+    # Sec. 2.1 (Thirion's regularisation): the Gaussian acts on the whole
+    # displacement field u + du, not on the update du alone.  With S = M
+    # constant, W - S and every gradient vanish, so du = 0 (Q7) and one
+    # iteration must give G_sigma * u for a rough, nonzero u; smoothing only
+    # du would leave u unchanged.
+    dims = (11, 9, 8)
+    vol = np.full(dims[::-1], -850.0)
+    u = np.stack([random_volume(dims, seed=41 + c) * 3.0 - 1.5 for c in range(3)])
+    for sigma in (1.0, 0.6):
+        un, red = oracle.iterate(variant, vol, vol.copy(), u, sigma=sigma, alpha=0.4)
+        for c in range(3):
+            np.testing.assert_allclose(un[c], _brute_gauss(u[c], sigma), rtol=0, atol=1e-12)
+        assert red[0] == 0.0 and red[1] == 0.0
+        assert red[2] == pytest.approx(np.sqrt((u ** 2).sum(axis=0)).sum(), rel=1e-13)
+        assert np.abs(un - u).max() > 0.1
+
+
 def test_inverse_consistent_is_antisymmetric():
     # Eq. (6) treats S and M symmetrically: registering (M, S) gives exactly -h
     S, M = make_blob_pair((16, 14, 12), (1.0, -0.5, 0.25), seed=3, n_blobs=20, sigma_vox=3.0)
