@@ -65,6 +65,11 @@ typedef enum {
     DIR_INVERSE_CONSISTENT = 5  /* Eq. (6): both images deformed toward a mid-space */
 } dir_variant;
 
+/* Element types.  DIR_F16 keeps its number for compatibility of the enum but
+   is accepted by no call of this build (DIR_EUNSUPPORTED): images are exact as
+   int16 HU, gradients are recomputed in registers and never stored, and a
+   half-precision field would sit between DIR_F32 and DIR_BF16 without a use
+   the paper's workloads need. */
 typedef enum { DIR_F32 = 0, DIR_I16 = 1, DIR_F16 = 2, DIR_BF16 = 3, DIR_F64 = 4 } dir_dtype;
 
 typedef struct {
@@ -81,21 +86,33 @@ typedef struct {
                                     (default) or DIR_BF16 (half the field bytes, arithmetic
                                     still FP32; only with precision DIR_F32) */
     const float* init_field;     /* NULL, or a DEVICE pointer to a level-0 field (3*N floats,
-                                    voxels) to start from; only with levels == 1 */
+                                    voxels) to start from; only with levels == 1 (DIR_EINVAL
+                                    otherwise): the paper starts the coarsest level from
+                                    zero (Sec. 2.3) and defines no restriction of a fine
+                                    field to the coarse grids, so a starting field is taken
+                                    only where it needs none */
     int use_graph;               /* 1 (default): capture the whole registration in a CUDA graph
                                     on the first dir_register and replay it afterwards */
     int timing;                  /* 1: time every force and smoothing launch at the finest level
                                     with CUDA events (reported in dir_stats); default 0 */
     dir_dtype precision;         /* arithmetic and storage of images and fields on the device:
-                                    DIR_F32 (default, the production path) or DIR_F64 (the same
-                                    kernels in double precision, for verification against an
-                                    FP64 reference where the iteration is ill-conditioned) */
+                                    DIR_F32 (default, the production path) or DIR_F64 (double
+                                    precision for verification against an FP64 reference; it
+                                    runs the plain-load kernels of plain_kernels = 1 in double,
+                                    not the TMA-tiled single-precision kernels) */
     int fuse;                    /* for Eqs. (1)-(2) without the stop test, with FP32 images and
                                     field: fold the Gaussian of iteration k into the force pass of
                                     iteration k+1 (same arithmetic, one pass over the field per
                                     iteration).  0: never; 1: every level; 2 (default): the small
                                     levels that one block per SM covers in two-plane chunks
                                     (e.g. 64 x 64 x 25), where it is faster */
+    int plain_kernels;           /* 0 (default): the production kernels (TMA-fed bricks and
+                                    plane rings, packed smoothing, fused small levels).  1: the
+                                    plain-load kernels with the same per-voxel arithmetic and
+                                    no tiling -- one thread per voxel column reading global
+                                    memory, 32 x 8 smoothing tiles, never fused -- in single
+                                    precision: a reference for the tiling, halo and ring code
+                                    of the production kernels.  Slower; not for production. */
 } dir_params;
 
 typedef struct {
@@ -121,7 +138,11 @@ typedef struct {
 int dir_params_default(dir_params* p);
 
 /*
- * Creates a registration context for one static/moving pair.
+ * Creates a registration context for one static/moving pair: the problem
+ * statement of Sec. 2 (register the moving image M to the static image S; the
+ * result is a per-voxel displacement field on the static grid, applied to
+ * moving-image points as in Sec. 3.2).  Uploads the pair once; the pyramid
+ * (Sec. 2.3) is built on the device by dir_register.
  *   static_img, moving_img  dense volumes of image_dtype: DIR_F32, or DIR_I16 (integer
  *                           HU, kept as int16 at the finest level, exact; needs
  *                           precision DIR_F32), host memory, or device memory if
@@ -142,16 +163,20 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
 
 /*
  * Replaces the image pair of ctx with new volumes of the same dims and dtype
- * (same ownership rules as dir_create).  The field restarts from zero (or
+ * (same ownership rules as dir_create), keeping every device buffer and the
+ * captured registration graph: a resident context serves the next pair of the
+ * same size (the problem statement of Sec. 2 for a new pair).  The field restarts from zero (or
  * init_field) at the next dir_register.
  */
 int dir_load(dir_ctx* ctx, const void* static_img, const void* moving_img, dir_dtype image_dtype,
              int on_device);
 
 /*
- * Runs the whole registration: pyramid build, then for each level (coarsest
- * first) the field up-sampling and the iterations, then (for Eq. 6) the
- * inversion of the mid-space field into the static-grid field.  Waits for
+ * Runs the whole registration: pyramid build (Sec. 2.3), then for each level
+ * (coarsest first) the field up-sampling (Sec. 2.3) and the iterations (warp,
+ * Sec. 2.5; force and update, Eqs. 1-6; Gaussian smoothing of the total field,
+ * Secs. 2.1 and 2.5; reductions and optional stop test, Sec. 2.4), then (for
+ * Eq. 6) the inversion of the mid-space field into the static-grid field.  Waits for
  * completion and fills *stats_out if it is not NULL.
  */
 int dir_register(dir_ctx* ctx, dir_stats* stats_out);
@@ -162,6 +187,8 @@ int dir_register_async(dir_ctx* ctx);
 int dir_sync(dir_ctx* ctx, dir_stats* stats_out);
 
 /*
+ * The result of the registration (Sec. 2: the displacement of every static
+ * voxel; Sec. 3.2 applies it to landmark points in mm).
  * Copies the registered static-grid field (3*N floats, planar, dense) to out,
  * a host pointer or, if out_on_device != 0, a device pointer.  in_mm != 0
  * multiplies each component by the voxel spacing of its axis.
@@ -173,6 +200,8 @@ int dir_get_field(dir_ctx* ctx, float* out, int in_mm, int out_on_device);
 int dir_get_field_f64(dir_ctx* ctx, double* out, int in_mm, int out_on_device);
 
 /*
+ * The quantities of the Sec. 2.4 stopping criterion: the relative norm
+ * l(n) = sum|du(n+1)| / sum|u(n)| is out[3t+1] / out[3t+2].
  * Per-iteration reductions of the last registration, in the order run
  * (coarsest level first): out[3*t + 0] = mean (W - S)^2 (for Eq. 6 the mean
  * squared difference of the two warped images), out[3*t + 1] = sum |du|,
@@ -183,8 +212,10 @@ int dir_get_field_f64(dir_ctx* ctx, double* out, int in_mm, int out_on_device);
 int dir_get_history(dir_ctx* ctx, double* out, int max_iters);
 
 /*
- * Warps an image on the static grid's dims by the registered field:
- * img_out(x) = img_in(x + u(x)), trilinear, clamped (Sec. 2.5).  img_in and
+ * Warps an image on the static grid's dims by the registered field, with the
+ * software trilinear interpolation of Sec. 2.5 (clamped coordinates):
+ * img_out(x) = img_in(x + u(x)).  With img_in = M this is the deformed moving
+ * image that the paper compares with S (Sec. 3.3).  img_in and
  * img_out are dense volumes of dtype dt (DIR_F32 in this build), both host or
  * both device (on_device != 0).
  */

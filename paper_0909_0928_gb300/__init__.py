@@ -45,7 +45,7 @@ class DirParams(C.Structure):
                 ("alpha", C.c_double), ("stop_mode", C.c_int), ("eps", C.c_double),
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
                 ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
-                ("precision", C.c_int), ("fuse", C.c_int)]
+                ("precision", C.c_int), ("fuse", C.c_int), ("plain_kernels", C.c_int)]
 
 
 class DirStats(C.Structure):
@@ -267,10 +267,21 @@ def dir_warp(ctx, img_in, img_out, dtype=DIR_F32, on_device=False):
 
 def dir_register_noalloc(static_img, moving_img, dims, variant=DIR_PASSIVE,
                          params: DirParams | None = None, field_out=None, stream=None) -> DirStats:
-    """Registration without device allocation (torch CUDA tensors in and out):
-    scratch comes from the library's static 48 MiB device array."""
+    """Registration without device allocation: float32 torch CUDA tensors of
+    nx*ny*nz voxels in, the static-grid field (3*N float32, voxels) written
+    into `field_out`, scratch from the library's static 48 MiB device array."""
+    if field_out is None:
+        raise ValueError("dir_register_noalloc: field_out (3*N float32 CUDA tensor) is required")
     st = DirStats()
     d = (C.c_int * 3)(*[int(x) for x in dims])
+    n = d[0] * d[1] * d[2]
+    _check_buffer(static_img, n, 4, "static_img")
+    _check_buffer(moving_img, n, 4, "moving_img")
+    _check_buffer(field_out, 3 * n, 4, "field_out")
+    for name, t in (("static_img", static_img), ("moving_img", moving_img),
+                    ("field_out", field_out)):
+        if not _is_torch(t) or not str(t.dtype).endswith("float32"):
+            raise ValueError(f"dir_register_noalloc: {name} must be a float32 torch CUDA tensor")
     rc = _lib.dir_register_noalloc(_ptr(static_img, True), _ptr(moving_img, True), C.byref(d),
                                    int(variant), C.byref(params) if params is not None else None,
                                    _ptr(field_out, True), _stream_handle(stream), C.byref(st))

@@ -240,6 +240,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
     c->launches = 0;
     const int L = c->levels;
     const bool f64 = c->fp64;
+    const bool plain = c->p.plain_kernels != 0;
     CK(c, cudaMemsetAsync(c->red, 0, sizeof(double) * 3 * (size_t)(c->total_iters > 0 ? c->total_iters : 1), s));
     CK(c, cudaMemsetAsync(c->ctl, 0x7f, sizeof(int) * (size_t)L, s));
     CK(c, cudaMemsetAsync(c->derr, 0, sizeof(int), s));
@@ -261,7 +262,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.in_type = c->img_type(l - 1);
             sa.out_type = c->real_type;
             sa.zchunk = 0;
-            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
+            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
             CK(c, dirk::launch_decimate(f64, c->B, gf, img ? c->lv[l].M : c->lv[l].S, gc, s));
             c->launches += 2;
         }
@@ -320,7 +321,8 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         // schedule keeps more blocks in flight (measured on 256x256x100)
         const bool fuse_here =
             c->p.fuse == 1 || (c->p.fuse == 2 && dirk::fused_small_level(g, c->num_sms));
-        const bool fused = fuse_here && c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
+        const bool fused = fuse_here && !plain && c->p.stop_mode == 0 &&
+                           dirk::fused_supported(c->variant) &&
                            c->field_type == c->real_type && c->img_type(l) == c->real_type;
         if (fused && n > 0) {
             // iteration 0 from u, iterations 1..n-1 from the previous v with the
@@ -335,7 +337,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     fa.v = vbuf;
                     fa.red = c->red + 3 * (size_t)row;
                     fa.iter = it;
-                    CK(c, dirk::launch_force(c->variant, f64, fa, s));
+                    CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
                 } else {
                     dirk::FusedArgs ua;
                     ua.S = c->lv[l].S;
@@ -362,7 +364,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     sa.in = vbuf;
                     sa.out = spare;
                     sa.iter = it;
-                    CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
+                    CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
                     c->launches += 1;
                     if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
                     cur = spare;
@@ -381,7 +383,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             fa.v = oth;
             fa.red = c->red + 3 * (size_t)row;
             fa.iter = it;
-            CK(c, dirk::launch_force(c->variant, f64, fa, s));
+            CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
             c->launches += 1;
             if (c->p.stop_mode == 1) {
                 CK(c, dirk::launch_stop_test(c->red, c->lhist, row, c->level_first[lc],
@@ -392,7 +394,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.in = oth;
             sa.out = cur;
             sa.iter = it;
-            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s));
+            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
             c->launches += 1;
             if (timed) {
                 if (record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -463,6 +465,7 @@ static int validate_params(const dir_params* p) {
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
     if (p->fuse < 0 || p->fuse > 2) return DIR_EINVAL;
+    if (p->plain_kernels != 0 && p->plain_kernels != 1) return DIR_EINVAL;
     return DIR_OK;
 }
 
@@ -501,6 +504,7 @@ int dir_params_default(dir_params* p) {
     p->timing = 0;
     p->precision = DIR_F32;
     p->fuse = 2;
+    p->plain_kernels = 0;
     return DIR_OK;
 }
 
@@ -1089,7 +1093,9 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {
             fa.depth = d;
             float ms = 0.0f;
-            rc = timed([&]() { return dirk::launch_force(c->variant, c->fp64, fa, c->stream); }, &ms);
+            rc = timed([&]() {
+                return dirk::launch_force(c->variant, c->fp64, fa, c->stream, c->p.plain_kernels != 0);
+            }, &ms);
             if (rc == DIR_OK && ms < best) {
                 best = ms;
                 best_d = d;
@@ -1115,7 +1121,9 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         for (int k = 0; k < nc && rc == DIR_OK; ++k) {
             sa.zchunk = cand[k];
             float ms = 0.0f;
-            rc = timed([&]() { return dirk::launch_smooth(c->fp64, sa, c->num_sms, c->stream); }, &ms);
+            rc = timed([&]() {
+                return dirk::launch_smooth(c->fp64, sa, c->num_sms, c->stream, c->p.plain_kernels != 0);
+            }, &ms);
             if (rc == DIR_OK && ms < best) {
                 best = ms;
                 best_z = cand[k];
@@ -1293,6 +1301,11 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
          cudaStreamSynchronize(c.stream) != cudaSuccess))
         rc = DIR_ECUDA;
     if (rc != DIR_OK) {
+        // work queued before the failure may still be writing the shared
+        // scratch: wait for it (its status is already reported by rc) so that
+        // the next serialised call does not race with it
+        cudaStreamSynchronize(c.stream);
+        cudaGetLastError();
         if (!c.err.empty()) g_create_error = c.err;
         return rc;
     }

@@ -15,20 +15,21 @@ int force_brick_depth(const Grid3& g, int min_blocks) {
     return 1;
 }
 
-cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s) {
+cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s, bool plain) {
     if (fp64) {
         if (a.img_type != kStoreF64 || a.field_type != kStoreF64) return cudaErrorInvalidValue;
         return launch_force_f64(variant, a, s);
     }
     if (a.img_type == kStoreI16) {
-        const cudaError_t e = launch_force_tma(variant, a, s);  // Eqs. 1-2: TMA-fed bricks
+        // TMA-fed bricks (Eqs. 1-6) unless the plain kernel is asked for
+        const cudaError_t e = plain ? cudaErrorNotSupported : launch_force_tma(variant, a, s);
         if (e != cudaErrorNotSupported) return e;
         return launch_force_i16(variant, a, s);
     }
     if (a.img_type != kStoreF32) return cudaErrorInvalidValue;
     if (a.field_type == kStoreBF16) return launch_force_bf16(variant, a, s);
     if (a.field_type == kStoreF32) {
-        const cudaError_t e = launch_force_tma(variant, a, s);  // Eqs. 1-2: TMA-fed bricks
+        const cudaError_t e = plain ? cudaErrorNotSupported : launch_force_tma(variant, a, s);
         if (e != cudaErrorNotSupported) return e;
         return launch_force_f32(variant, a, s);
     }

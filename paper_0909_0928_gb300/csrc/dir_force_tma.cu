@@ -185,14 +185,9 @@ static cudaError_t launch_ft(const ForceArgs& a, cudaStream_t s) {
     using F = FTGeom<FTZ, V, TI>;
     CUtensorMap umap, smap, mmap;
     if (!make_force_maps<TI>(&umap, &smap, &mmap, a, FTZ)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(force_tma_kernel<V, FTZ, TI>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    const cudaError_t e = setup_kernel(setup, force_tma_kernel<V, FTZ, TI>, F::SMEM);
+    if (e != cudaSuccess) return e;
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
     force_tma_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), F::SMEM, s>>>(umap, smap, mmap, a);
     return cudaGetLastError();
@@ -413,14 +408,9 @@ static cudaError_t launch_fg(const ForceArgs& a, cudaStream_t s) {
     using F = FGGeom<FTZ, V, TI>;
     CUtensorMap umap, smap, mmap;
     if (!make_gm_maps<TI>(&umap, &smap, &mmap, a, FTZ)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(force_tma_gm_kernel<V, FTZ, TI>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    const cudaError_t e = setup_kernel(setup, force_tma_gm_kernel<V, FTZ, TI>, F::SMEM);
+    if (e != cudaSuccess) return e;
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
     force_tma_gm_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), F::SMEM, s>>>(umap, smap, mmap, a);
     return cudaGetLastError();

@@ -157,16 +157,10 @@ static cudaError_t launch_rv(const FusedArgs& a, int num_sms, cudaStream_t s) {
     using F = FusedGeom<Real, R>;
     CUtensorMap map;
     if (!make_plane_map<Real, R, 3>(&map, a.vin, a.g, 3)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            fused_kernel<Real, R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<Real, R, V>, FUSED_NT,
-                                                  F::SMEM);
+    const cudaError_t e = setup_kernel(setup, fused_kernel<Real, R, V>, F::SMEM, FUSED_NT, &per_sm);
+    if (e != cudaSuccess) return e;
     const int zc = stencil_zchunk(a.g, per_sm, num_sms);
     const dim3 grid((a.g.nx + STX - 1) / STX, (a.g.ny + STY - 1) / STY, (a.g.nz + zc - 1) / zc);
     fused_kernel<Real, R, V><<<grid, dim3(FUSED_NT, 1, 1), F::SMEM, s>>>(map, a, zc);
@@ -415,16 +409,10 @@ static cudaError_t launch_f2(const FusedArgs& a, int num_sms, cudaStream_t s) {
     using F = F2Geom<R>;
     CUtensorMap vmap, smap;
     if (!make_f2_maps<R>(&vmap, &smap, a)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    static int per_sm = 1;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fused2_kernel<R, V>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused2_kernel<R, V>, F2T, F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    int per_sm = 1;
+    const cudaError_t e = setup_kernel(setup, fused2_kernel<R, V>, F::SMEM, F2T, &per_sm);
+    if (e != cudaSuccess) return e;
     const int tiles = ((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + S2Y - 1) / S2Y);
     long long chunks = ((long long)(per_sm < 1 ? 1 : per_sm) * num_sms) / tiles;
     if (chunks < 1) chunks = 1;
@@ -649,13 +637,9 @@ static cudaError_t launch_fs(const FusedArgs& a, cudaStream_t s) {
     };
     if (!enc4(&vmap, a.vin, vdims, vbox) || !enc4(&smap, a.S, sdims, sbox))
         return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            fused_small_kernel<R, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    const cudaError_t e = setup_kernel(setup, fused_small_kernel<R, V>, F::SMEM);
+    if (e != cudaSuccess) return e;
     const dim3 grid((g.nx + S2X - 1) / S2X, (g.ny + S2Y - 1) / S2Y, (g.nz + FZC - 1) / FZC);
     fused_small_kernel<R, V><<<grid, dim3(F2T, 1, 1), F::SMEM, s>>>(vmap, smap, a);
     return cudaGetLastError();

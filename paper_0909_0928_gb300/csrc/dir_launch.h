@@ -33,7 +33,10 @@ struct ForceArgs {
                          // this many linear indices ahead
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
 };
-cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s);
+// plain = true: the plain-load force_kernel even where a TMA-fed kernel exists
+// (the same per-voxel arithmetic without the tiling; a cross-check of it)
+cudaError_t launch_force(int variant, bool fp64, const ForceArgs& a, cudaStream_t s,
+                         bool plain = false);
 int force_brick_depth(const Grid3& g, int min_blocks);
 
 // Separable Gaussian (Sec. 2.5 low-pass filter), x then y then z, replicate
@@ -51,7 +54,10 @@ struct SmoothArgs {
     int out_type;        // storage of out
     int zchunk;          // planes per block; 0 = one wave of resident blocks
 };
-cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s);
+// plain = true: the 32 x 8 tile kernel (smooth_kernel) for every storage type
+// instead of the packed single-precision kernels
+cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s,
+                          bool plain = false);
 
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
 // force kernel's work, v = u - dr(u); red as for ForceArgs.

@@ -318,13 +318,9 @@ static cudaError_t launch_ss(const SmoothArgs& a, cudaStream_t s) {
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            smooth_small_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, F::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    const cudaError_t e = setup_kernel(setup, smooth_small_kernel<R>, F::SMEM);
+    if (e != cudaSuccess) return e;
     const dim3 grid((g.nx + S2X - 1) / S2X, (g.ny + S2Y - 1) / S2Y, (g.nz + SZC - 1) / SZC);
     smooth_small_kernel<R><<<grid, dim3(SST, 1, 1), F::SMEM, s>>>(map, a);
     return cudaGetLastError();
@@ -363,17 +359,10 @@ static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     using G = S2Smem<R, TY>;
     CUtensorMap map;
     if (!make_s2_map<R, TY>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    static int per_sm = 1;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(smooth2_kernel<R, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth2_kernel<R, TY>, 8 * TY,
-                                                          G::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
+    int per_sm = 1;
+    const cudaError_t e = setup_kernel(setup, smooth2_kernel<R, TY>, G::SMEM, 8 * TY, &per_sm);
+    if (e != cudaSuccess) return e;
     int zc = a.zchunk > 0 ? a.zchunk : s2_zchunk(a.g, TY, per_sm, num_sms, a.ncomp);
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
@@ -396,17 +385,11 @@ static cudaError_t launch_rt(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     using G = StencilGeom<Real, R, 1, 8, TIN>;
     CUtensorMap map;
     if (!make_plane_map<Real, R, 1, TIN>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(smooth_kernel<Real, R, TIN, TOUT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   G::BASE_SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static KernelSetup setup;  // per instantiation
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smooth_kernel<Real, R, TIN, TOUT>,
-                                                  G::YT, G::BASE_SMEM);
+    const cudaError_t e =
+        setup_kernel(setup, smooth_kernel<Real, R, TIN, TOUT>, G::BASE_SMEM, G::YT, &per_sm);
+    if (e != cudaSuccess) return e;
     int zc = a.zchunk > 0 ? a.zchunk : stencil_zchunk(a.g, per_sm, num_sms, a.ncomp);
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
@@ -430,13 +413,15 @@ static cudaError_t launch_types(const SmoothArgs& a, int num_sms, cudaStream_t s
     }
 }
 
-cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s,
+                          bool plain) {
     if (a.ncomp != 1 && a.ncomp != 3) return cudaErrorInvalidValue;
     if (fp64) {
         if (a.in_type != kStoreF64 || a.out_type != kStoreF64) return cudaErrorInvalidValue;
         return launch_types<double, double, double>(a, num_sms, s);
     }
     if (a.in_type == kStoreF32 && a.out_type == kStoreF32) {
+        if (plain) return launch_types<float, float, float>(a, num_sms, s);
         if (a.ncomp == 3 && a.zchunk == 0 && smooth_small_level(a.g, num_sms)) {
             switch (a.taps.R) {  // small levels: all planes of a chunk at once
                 case 1: return launch_ss<1>(a, s);

@@ -14,6 +14,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "dir_common.cuh"
@@ -264,6 +266,48 @@ inline EncodeTiledFn encode_fn() {
             fn = reinterpret_cast<EncodeTiledFn>(p);
     }
     return fn;
+}
+
+// One-time set-up of a kernel on each device: the opt-in to more than 48 KB of
+// dynamic shared memory (cudaFuncSetAttribute acts on the function for the
+// current device only) and, if asked, its resident blocks per SM.  One
+// KernelSetup per kernel instantiation; safe to call from several host
+// threads and devices.
+struct KernelSetup {
+    static constexpr int kMaxDevices = 64;
+    std::atomic<unsigned long long> done{0};  // bit d: set up on device d
+    int per_sm[kMaxDevices] = {};
+};
+
+inline std::mutex& kernel_setup_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+template <typename Fn>
+inline cudaError_t setup_kernel(KernelSetup& st, Fn* fn, int smem, int threads = 0,
+                                int* per_sm_out = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= KernelSetup::kMaxDevices) return cudaErrorInvalidDevice;
+    const unsigned long long bit = 1ull << dev;
+    if (!(st.done.load(std::memory_order_acquire) & bit)) {
+        std::lock_guard<std::mutex> lock(kernel_setup_mutex());
+        if (!(st.done.load(std::memory_order_relaxed) & bit)) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            int n = 1;
+            if (threads > 0) {
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem);
+                if (e != cudaSuccess) return e;
+            }
+            st.per_sm[dev] = n < 1 ? 1 : n;
+            st.done.fetch_or(bit, std::memory_order_release);
+        }
+    }
+    if (per_sm_out) *per_sm_out = st.per_sm[dev];
+    return cudaSuccess;
 }
 
 // Tensor map of a pitched (x, y, z, component) array of ncomp components with

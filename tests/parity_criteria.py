@@ -1,25 +1,38 @@
-"""The single-precision parity criterion, shared by the GPU parity tests and
-the CPU test that calibrates it (tests/test_oracle_twin.py).
+"""Parity criteria of the GPU path against the FP64 oracle, shared by the GPU
+parity tests and the CPU tests that calibrate them (tests/test_oracle_twin.py).
 
-The demons iteration amplifies rounding unevenly, so the FP32 GPU field is
-compared with the FP64 oracle against the oracle's own sensitivity: the
-per-voxel spread of oracle runs whose state is perturbed at rounding size
-(`oracle.register(..., probe_rel, probe_seed)`).
+The bar (BASELINE the benchmark spec): max |du| <= 1e-3 voxel and relative RMS of the
+warped image <= 1e-4, at a fixed iteration count.
 
-(1) Voxels whose 7^3 neighbourhood (the footprint of the sigma = 1 Gaussian,
-    through which rounding spreads between iterations) keeps the spread within
-    bar * COND must meet the bar.
-(2) Over the whole volume each quantile of the error (median up to the
-    maximum) must stay within SHADOW times the same quantile of the spread,
-    plus bar * COND: the spread of a few probes predicts the size of the
-    deviation a single-precision run has, not its exact place.  SHADOW is
-    calibrated by an independent single-precision implementation (the NumPy
-    twin in float32), which deviates from the oracle by up to about five times
-    the probes' spread at the 99th percentile on small ragged volumes.
+strict_check: the bar on EVERY voxel and the warped image over the whole
+    volume.  Used wherever the oracle's own single-precision spread stays
+    within bar / 10 everywhere (short schedules: the iteration amplifies
+    rounding, and a long enough run leaves that regime for any FP32 field).
+
+shadow_check: where the oracle is ill-conditioned (long schedules at full
+    size) the FP32 field is compared against the oracle's own sensitivity: the
+    per-voxel spread of oracle runs whose state is perturbed at rounding size
+    (`oracle.register(..., probe_rel, probe_seed)`).
+    (1) Voxels whose 7^3 neighbourhood (the footprint of the sigma = 1
+        Gaussian, through which rounding spreads between iterations) keeps the
+        spread within bar * COND (the conditioned set) must meet the bar.
+    (2) Over the whole volume each quantile of the error (median up to the
+        maximum) must stay within SHADOW times the same quantile of the
+        spread, plus bar * COND: the spread of a few probes predicts the size
+        of the deviation a single-precision run has, not its exact place.
+        SHADOW is calibrated by an independent single-precision
+        implementation (the NumPy twin in float32), which deviates from the
+        oracle by up to about five times the probes' spread at the 99th
+        percentile on small ragged volumes.
+w_check: the warped image on every case: rel-RMS over the whole volume within
+    TOL_W, or, where the probes themselves move the warped image by more than
+    TOL_W * COND, within SHADOW times their largest rel-RMS.
 """
 import numpy as np
 
-COND = 0.01       # conditioned: the neighbourhood's spread within bar * COND
+TOL_U = 1e-3      # voxel
+TOL_W = 1e-4      # relative RMS of the warped image
+COND = 0.1        # conditioned: the neighbourhood's spread within bar * COND
 SHADOW = 10.0     # error quantiles within SHADOW x the spread quantiles
 QUANTILES = (0.5, 0.9, 0.99, 0.999, 0.9999, 1.0)
 
@@ -27,6 +40,20 @@ QUANTILES = (0.5, 0.9, 0.99, 0.999, 0.9999, 1.0)
 def conditioned(spread, bar):
     from scipy.ndimage import maximum_filter
     return maximum_filter(spread, size=7, mode="nearest") <= bar * COND
+
+
+def rel_rms(a, ref):
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.sqrt(np.mean((a - ref) ** 2)) / max(np.sqrt(np.mean(ref ** 2)), 1e-30))
+
+
+def strict_check(err, label, bar=TOL_U):
+    """max |du| <= bar on every voxel (err: per-voxel max over components)."""
+    worst = float(err.max())
+    assert worst <= bar, (f"{label}: max|du| {worst:.3e} (bar {bar:g}); "
+                          f"{int((err > bar).sum())} voxels above")
+    return worst
 
 
 def shadow_check(err, spread, bar, label, min_cond=0.0):
@@ -45,12 +72,32 @@ def shadow_check(err, spread, bar, label, min_cond=0.0):
     return ill
 
 
-def fp32_spread(oracle, S, M, variant, levels, iters, ref_u, alpha=0.4, sigma=1.0):
+def w_check(W, W_ref, label, probe_w_rel=0.0):
+    """Warped image over the whole volume: rel-RMS within TOL_W, or within
+    SHADOW x the probes' own rel-RMS where that exceeds TOL_W * COND.
+    Returns (rel-RMS, bar)."""
+    rel = rel_rms(W, W_ref)
+    bar = TOL_W if probe_w_rel <= TOL_W * COND else max(TOL_W, SHADOW * probe_w_rel)
+    assert rel <= bar, f"{label}: rel-RMS(W) {rel:.3e} (bar {bar:.1e})"
+    return rel, bar
+
+
+FP32_PROBES = ((None, 1.0), (0, 2.0 ** -24), (0, -(2.0 ** -24)))  # (seed, rel); None = ROUND32
+
+
+def fp32_spread(oracle, S, M, variant, levels, iters, ref_u, alpha=0.4, sigma=1.0,
+                with_w=False):
     """Spread of the single-precision probes: the state stored in float
-    (oracle.ROUND32) and the coherent +-2^-24 nudge."""
+    (oracle.ROUND32) and the coherent +-2^-24 nudge.  With with_w, also the
+    largest rel-RMS by which they move the warped image oracle.warp(M, u)."""
     spread = np.zeros(S.shape)
-    for seed, rel in ((oracle.ROUND32, 1.0), (0, 2.0 ** -24), (0, -(2.0 ** -24))):
+    w_rel = 0.0
+    W_ref = oracle.warp(M, ref_u) if with_w else None
+    for seed, rel in FP32_PROBES:
         up = oracle.register(S, M, variant=variant, levels=levels, iters=iters, alpha=alpha,
-                             sigma=sigma, probe_rel=rel, probe_seed=seed)["u"]
+                             sigma=sigma, probe_rel=rel,
+                             probe_seed=oracle.ROUND32 if seed is None else seed)["u"]
         spread = np.maximum(spread, np.abs(up - ref_u).max(axis=0))
-    return spread
+        if with_w:
+            w_rel = max(w_rel, rel_rms(oracle.warp(M, up), W_ref))
+    return (spread, w_rel) if with_w else spread

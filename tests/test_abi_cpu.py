@@ -104,3 +104,26 @@ def test_binding_refuses_buffers_of_the_wrong_size_or_width(dl):
         dl.dir_create(S, S, (4, 4, 4), (1, 1, 1), image_dtype=dl.DIR_I16)
     with pytest.raises(ValueError):
         dl.dir_create(S, S, (4, 4, 5), (1, 1, 1))
+
+
+def test_noalloc_binding_checks_buffers_before_the_call(dl):
+    # the library reads N floats from each image and writes 3N to field_out:
+    # wrong sizes, widths, host memory or a missing output never reach it
+    torch = pytest.importorskip("torch")
+    dims = (8, 6, 4)
+    n = 8 * 6 * 4
+    good = torch.zeros(n, dtype=torch.float32)
+    with pytest.raises(ValueError):
+        dl.dir_register_noalloc(good, good, dims, 0, None, None)
+    with pytest.raises(ValueError):
+        dl.dir_register_noalloc(torch.zeros(n - 1), good, dims, 0, None, torch.zeros(3 * n))
+    with pytest.raises(ValueError):
+        dl.dir_register_noalloc(good, torch.zeros(n, dtype=torch.int16), dims, 0, None,
+                                torch.zeros(3 * n))
+    with pytest.raises(ValueError):
+        dl.dir_register_noalloc(good, good, dims, 0, None, torch.zeros(2 * n))
+    with pytest.raises(ValueError):   # correct sizes, but host tensors
+        dl.dir_register_noalloc(good, good, dims, 0, None, torch.zeros(3 * n))
+    with pytest.raises(ValueError):   # numpy arrays are host memory
+        dl.dir_register_noalloc(np.zeros(n, np.float32), np.zeros(n, np.float32), dims, 0,
+                                None, np.zeros(3 * n, np.float32))

@@ -82,3 +82,29 @@ def test_the_criterion_rejects_a_slip():
     err = np.abs(u - ref["u"]).max(axis=0)
     with pytest.raises(AssertionError):
         shadow_check(err, spread, 1e-3, "slipped twin")
+
+
+def test_the_criteria_reject_a_slip_at_full_size(full_phantom):
+    # The same kind of slip, planted in the oracle (a smoothing width 2 % too
+    # small: the same 7 taps, slightly different values), on the 256 x 256 x 100
+    # phantom: the every-voxel check of the short full-size schedules and the
+    # shadow check of the long 200/100/50 schedule must both reject it, although
+    # at full size the latter's conditioned set is a small part of the volume.
+    from parity_criteria import TOL_U, fp32_spread, rel_rms, shadow_check, strict_check
+    S, M = full_phantom["S"], full_phantom["M"]
+    short = dict(variant=0, levels=1, iters=[10])
+    ref = oracle.register(S, M, **short)["u"]
+    slip = oracle.register(S, M, sigma=0.98, **short)["u"]
+    err = np.abs(slip - ref).max(axis=0)
+    with pytest.raises(AssertionError):
+        strict_check(err, "slipped oracle, 1 level x 10")
+    print(f"short schedule: slip max|du| {err.max():.2e}, "
+          f"rel-RMS(W) {rel_rms(oracle.warp(M, slip), oracle.warp(M, ref)):.1e}")
+    sched = dict(levels=3, iters=[200, 100, 50])
+    ref = oracle.register(S, M, variant=0, **sched)["u"]
+    spread = fp32_spread(oracle, S, M, 0, ref_u=ref, **sched)
+    slip = oracle.register(S, M, variant=0, sigma=0.98, **sched)["u"]
+    err = np.abs(slip - ref).max(axis=0)
+    with pytest.raises(AssertionError) as e:
+        shadow_check(err, spread, TOL_U, "slipped oracle, 200/100/50")
+    print(f"long schedule: {e.value}")

@@ -29,12 +29,19 @@ def _with_context(dl, S, M, variant, params):
         return reg.field()
 
 
-def test_noalloc_matches_allocating_path_on_consecutive_calls(dl):
+# the scratch layout changes with the element size of the field (2 bytes for
+# BF16, 8 for FP64, whose images are 8 bytes too), and the field export
+# converts from each of them
+FORMS = {"f32": {}, "bf16_field": {"field_dtype": 3}, "f64": {"precision": 4}}
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_noalloc_matches_allocating_path_on_consecutive_calls(dl, form):
     from phantom import SMALL, make_lung_phantom
     p = make_lung_phantom(SMALL)
     S, M = p["S"], p["M"]
     nz, ny, nx = S.shape
-    params = dl.dir_params_default(levels=2, iters=[8, 6])
+    params = dl.dir_params_default(levels=2, iters=[8, 6], **FORMS[form])
     St, Mt = torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda()
     out = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -50,7 +57,7 @@ def test_noalloc_matches_allocating_path_on_consecutive_calls(dl):
         want = _with_context(dl, S, M, variant, params)
         got = out.cpu().numpy()
         err = float(np.abs(got - want).max())
-        assert err <= TOL, f"variant {variant}: max |du| {err:.3e}"
+        assert err <= TOL, f"{form} variant {variant}: max |du| {err:.3e}"
         if variant == dl.DIR_INVERSE_CONSISTENT:
             # the first call on this device already looked up the scratch; this
             # one must not take device memory
