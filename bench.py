@@ -12,6 +12,7 @@ second of device time) with s per registration p50/p99 beside it.
   python bench.py --form batch       # 32 uneven int16 pairs: one graph vs 32 plain runs
   python bench.py --form study       # landmark accuracy per force law, alpha sweep, stop test
   python bench.py --form precision   # int16 images / BF16 field against the FP64 kernels
+  python bench.py --form serve       # Poisson request streams: plain queue vs continuous batching
 
 Prints one JSON line on rank 0.
 """
@@ -251,29 +252,28 @@ def run_reference(args):
 BATCH_PAIRS = 32
 
 
-def batch_pairs(n=BATCH_PAIRS, seed=3):
-    """Uneven int16 pairs cropped from one seeded 256 x 256 x 128 lung phantom
-    (RBF motion up to 12 mm, 20% compression of the lower lung): sizes uniform
-    in 96..256 x 96..256 x 48..128, passive or inverse-consistent at random."""
+def _batch_pair(k):
+    """Pair k of the batched form: seed 100 + k, dims drawn per axis uniformly
+    on multiples of 16 (96..256 x 96..256 x 48..128), RBF motion up to 12 mm
+    with 20% compression of the lower lung, int16 HU; passive for even k,
+    inverse consistent for odd k."""
     import numpy as np
     from phantom import PhantomSpec, SplitMix64Stream, make_lung_phantom
-    ph = make_lung_phantom(PhantomSpec(dims=(256, 256, 128), spacing=SPACING, seed=seed,
-                                       a_max_mm=12.0, compression=0.2,
-                                       compression_region="lower", n_landmarks=10))
-    S = np.round(ph["S"]).astype(np.int16)
-    M = np.round(ph["M"]).astype(np.int16)
-    rng = SplitMix64Stream(seed, sid=21)
-    out = []
-    for _ in range(n):
-        r = rng.uniform(7)
-        nx, ny = 96 + int(r[0] * 161), 96 + int(r[1] * 161)
-        nz = 48 + int(r[2] * 81)
-        x0, y0 = int(r[3] * (257 - nx)), int(r[4] * (257 - ny))
-        z0 = int(r[5] * (129 - nz))
-        sl = (slice(z0, z0 + nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
-        out.append((np.ascontiguousarray(S[sl]), np.ascontiguousarray(M[sl]),
-                    0 if r[6] < 0.5 else 5))
-    return out
+    r = SplitMix64Stream(100 + k, sid=21).uniform(3)
+    dims = (96 + 16 * int(r[0] * 11), 96 + 16 * int(r[1] * 11), 48 + 16 * int(r[2] * 6))
+    ph = make_lung_phantom(PhantomSpec(dims=dims, spacing=SPACING, seed=100 + k, a_max_mm=12.0,
+                                       compression=0.2, compression_region="lower",
+                                       n_landmarks=10))
+    return (np.round(ph["S"]).astype(np.int16), np.round(ph["M"]).astype(np.int16),
+            0 if k % 2 == 0 else 5)
+
+
+def batch_pairs(n=BATCH_PAIRS):
+    """The 32 seeded pairs of uneven sizes, generated on the host cores by a
+    pool started with spawn before any GPU work."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
+        return pool.map(_batch_pair, range(n))
 
 
 def run_batch(args):
@@ -306,6 +306,8 @@ def run_batch(args):
         return t_all / reps, done
 
     sequential(1)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     plain_ms, plain_done = sequential(args.steps)
     ref = []
     for (S, _, _), c in zip(pairs, ctxs):
@@ -328,6 +330,7 @@ def run_batch(args):
         if best is None or ms < per_branches[best]:
             best = br
         dl.dir_batch_destroy(b)
+    clk = clocks.stop()
     same = True
     for (S, _, _), c, f0 in zip(pairs, ctxs, ref):
         f = np.empty((3,) + S.shape, np.float32)
@@ -339,7 +342,9 @@ def run_batch(args):
     q = lambda xs, p: float(np.quantile(np.asarray(xs), p))
     line = {"mode": "batch", "pairs": n, "variants": {"passive": sum(v == 0 for *_, v in pairs),
                                                       "inverse_consistent": sum(v == 5 for *_, v in pairs)},
-            "sizes": "96..256 x 96..256 x 48..128 int16 HU crops, FP32 fields, 3 levels 200/100/50",
+            "sizes": "seeds 100-131, dims uniform on multiples of 16 in 96..256 x 96..256 x "
+                     "48..128, int16 HU, FP32 fields, 3 levels 200/100/50",
+            "dims": [list(S.shape[::-1]) for S, _, _ in pairs],
             "voxel_updates": vu,
             "plain_sequential": {"ms": plain_ms, "volumes_per_s": n / (plain_ms / 1e3),
                                  "voxel_updates_per_s": vu / (plain_ms / 1e3),
@@ -351,7 +356,7 @@ def run_batch(args):
                         "completion_p50_ms": bms, "completion_p99_ms": bms,
                         "per_branch_count_ms": per_branches},
             "speedup_vs_plain": plain_ms / bms, "fields_identical": same,
-            "autotune_s": tune_s, "tuned_shapes_first_pair": shapes[0]}
+            "autotune_s": tune_s, "tuned_shapes_first_pair": shapes[0], "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0 if same else 1
 
@@ -416,6 +421,8 @@ def run_study(args):
                 "iters_run": list(st.iters_run[:LEVELS]), "mse_final": st.mse_final,
                 "relnorm_final": st.relnorm_final, "correlation": correlation(W)}
 
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     out["variants"] = {VARIANT_NAMES[v]: run(v) for v in range(6)}
     out["alpha_sweep_adjusted_double"] = {str(a): run(4, alpha=a)
                                           for a in (0.1, 0.2, 0.4, 0.5, 1.0, 2.0, 3.0, 5.0)}
@@ -426,6 +433,7 @@ def run_study(args):
     out["finest_iterations_passive"] = {
         str(k): run(0, iters=[ITERS[0], ITERS[1], k], reps=0)
         for k in (0, 5, 10, 20, 30, 50, 70, 90)}
+    out["clocks"] = clocks.stop()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -454,6 +462,8 @@ def run_precision(args):
     # bytes per voxel-update of the finest-level two-kernel iteration
     bpv = {("f32", "f32"): 56, ("i16", "f32"): 52, ("f32", "bf16"): 32, ("i16", "bf16"): 28}
     out = {"mode": "precision", "workload": "256x256x100 lung phantom rounded to int16 HU, passive"}
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     for sched_name, levels, iters in (("single_scale_50", 1, [50]), ("pyramid_200_100_50", 3, ITERS)):
         def run(img, field, precision=dl.DIR_F32):
             S_d, M_d, dt = imgs[img]
@@ -480,7 +490,27 @@ def run_precision(args):
                 "median_du_vs_f64": float(np.median(err)),
                 "landmark_mm": {"mean": m, "sd": sd}}
         out[sched_name] = res
+    out["clocks"] = clocks.stop()
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving sweep (config 5): Poisson arrivals at 1 to 20 jobs/s of int16 HU
+    registrations, 128x128x64 .. 512x512x160, force law uniform over the six,
+    3 levels; a plain queue (one job at a time, fresh context each) against
+    continuous batching with fresh and with resident contexts.  One JSON line
+    per rate, clocks sampled over the whole sweep."""
+    import torch
+    from paper_0909_0928_gb300 import serve
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    lines = serve.sweep([1, 2, 5, 10, 20], jobs=args.steps, slots=8, seed=5)
+    clk = clocks.stop()
+    for line in lines:
+        line["clocks"] = clk
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -494,7 +524,8 @@ def main():
     ap.add_argument("--alpha", type=float, default=0.4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--form", default="plain", choices=["plain", "batch", "study", "precision"])
+    ap.add_argument("--form", default="plain",
+                    choices=["plain", "batch", "study", "precision", "serve"])
     ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2],
                     help="fold the Gaussian into the next force pass (Eqs. 1-2): 0 never, "
                          "1 every level, 2 (library default) the small levels")
@@ -510,6 +541,8 @@ def main():
         return run_study(args)
     if args.form == "precision":
         return run_precision(args)
+    if args.form == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch

@@ -1,16 +1,19 @@
-"""Registration serving loop with continuous batching.
+"""Registration serving loop with continuous batching and resident contexts.
 
 Requests (a static/moving pair, a force law, a schedule) arrive over time.  The
-server keeps a fixed number of slots, one CUDA stream each.  A waiting request
-is admitted as soon as a slot is free and its device footprint fits the HBM
-budget left by the jobs already resident; it then gets its own context
-(dir_create: images uploaded once, pyramid and fields resident on the device)
-and its registration is enqueued on the slot's stream (dir_register_async).
-Jobs on different slots overlap on the GPU; a job's completion is detected
-without blocking by a CUDA event recorded behind its work, after which its
-field is read back, its context freed and the slot handed to the next waiting
-request.  Every step of a registration runs in the library's kernels; this
-module only schedules.
+server runs at most `slots` registrations at once.  A waiting request is
+admitted as soon as a slot is free and its device footprint fits the HBM
+budget: if an idle context of the same volume size, image type, force law and
+schedule is resident, the pair is loaded into it (dir_load: the images are
+copied in, the pyramid, fields and captured registration graph stay on the
+device); otherwise a new context is created on a stream of its own
+(dir_create), after evicting idle contexts of other shapes, least recently
+used first, while the budget requires it.  The registration is enqueued on
+the context's stream (dir_register_async); jobs on different streams overlap
+on the GPU.  A job's completion is detected without blocking by a CUDA event
+recorded behind its work, after which its field is read back and its context
+returns to the idle pool for the next request of its shape.  Every step of a
+registration runs in the library's kernels; this module only schedules.
 
     python -m paper_0909_0928_gb300.serve --rates 1 2 5 10 20 --jobs 40
 
@@ -29,14 +32,16 @@ from dataclasses import field as dc_field
 
 import numpy as np
 
-from . import (DIR_F32, DIR_I16, DirParams, dir_create, dir_destroy, dir_get_field, dir_params_default,
-               dir_register_async, dir_sync)
+from . import (DIR_BF16, DIR_F32, DIR_F64, DIR_I16, DirParams, dir_create, dir_destroy,
+               dir_get_field, dir_load, dir_params_default, dir_register_async, dir_sync)
 
 
-def footprint_bytes(dims, levels: int, elem: int = 4) -> int:
-    """Device bytes one context holds: pyramid images (2 per level), two fields
-    of the finest size, plus a margin for staging and pitch padding."""
+def footprint_bytes(dims, levels: int, elem: int = 4, field_elem: int | None = None) -> int:
+    """Device bytes one context holds: pyramid images (2 per level, pitched
+    rows), two fields of the finest size, the staging buffer of the host field
+    read-back (3 N floats), plus a margin for reduction rows and padding."""
     nx, ny, nz = dims
+    fe = elem if field_elem is None else field_elem
     total = 0
     n0 = 0
     for lv in range(levels):
@@ -44,10 +49,23 @@ def footprint_bytes(dims, levels: int, elem: int = 4) -> int:
         n = px * ny * nz
         if lv == 0:
             n0 = n
-        total += 2 * n
+        total += 2 * n * elem
         nx, ny, nz = (nx + 1) // 2, (ny + 1) // 2, (nz + 1) // 2
-    total += 6 * n0
-    return int(total * elem * 1.05) + (4 << 20)
+    total += 6 * n0 * fe
+    stage = 3 * dims[0] * dims[1] * dims[2] * 4
+    return int((total + stage) * 1.05) + (4 << 20)
+
+
+def _params_key(p: DirParams) -> tuple:
+    return (p.levels, tuple(p.iters[: p.levels]), p.sigma, p.alpha, p.stop_mode, p.eps,
+            p.stop_window, p.field_dtype, p.use_graph, p.precision, p.fuse, p.plain_kernels)
+
+
+def request_footprint(req) -> int:
+    p = req.params
+    elem = 8 if p.precision == DIR_F64 else 4
+    fe = 2 if p.field_dtype == DIR_BF16 else elem
+    return footprint_bytes(req.dims, p.levels, elem, fe)
 
 
 @dataclass
@@ -76,19 +94,29 @@ class Request:
 
 
 class Server:
-    """Continuous-batching scheduler over `slots` CUDA streams."""
+    """Continuous-batching scheduler: at most `slots` registrations at once,
+    contexts resident between requests of the same shape."""
 
-    def __init__(self, slots: int = 8, hbm_budget_bytes: int | None = None, keep_fields=True):
+    def __init__(self, slots: int = 8, hbm_budget_bytes: int | None = None, keep_fields=True,
+                 reuse: bool = True):
         import torch
         self.torch = torch
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.slots = slots
         free, _total = torch.cuda.mem_get_info()
         self.budget = hbm_budget_bytes if hbm_budget_bytes is not None else int(free * 0.8)
-        self.in_use = 0
+        self.in_use = 0           # bytes of every resident context, busy or idle
         self.waiting: collections.deque[Request] = collections.deque()
-        self.running: dict[int, tuple] = {}  # slot -> (request, ctx, event, bytes)
+        self.running: list[tuple] = []   # (request, entry, event)
+        # idle contexts by shape key, least recently used first: entry =
+        # [ctx, stream, bytes, key]
+        self.idle: collections.OrderedDict[int, list] = collections.OrderedDict()
         self.finished: list[Request] = []
         self.keep_fields = keep_fields
+        self.reuse = reuse
+        self.created = 0
+        self.reused = 0
+        self.evicted = 0
+        self._next_id = 0
         self.t0 = time.perf_counter()
 
     def now(self) -> float:
@@ -97,35 +125,62 @@ class Server:
     def submit(self, req: Request):
         self.waiting.append(req)
 
+    @staticmethod
+    def _key(req) -> tuple:
+        return (req.dims, req.S.dtype == np.int16, req.variant, _params_key(req.params))
+
+    def _take_idle(self, key):
+        for eid, entry in self.idle.items():
+            if entry[3] == key:
+                del self.idle[eid]
+                return entry
+        return None
+
+    def _evict_for(self, need: int) -> bool:
+        """Free idle contexts, least recently used first, until `need` more
+        bytes fit; False if they cannot."""
+        while self.in_use + need > self.budget and self.idle:
+            _eid, (ctx, _stream, nbytes, _key) = self.idle.popitem(last=False)
+            dir_destroy(ctx)
+            self.in_use -= nbytes
+            self.evicted += 1
+        return self.in_use + need <= self.budget
+
     def _admit(self):
-        while self.waiting:
-            free_slots = [s for s in range(len(self.streams)) if s not in self.running]
-            if not free_slots:
-                return
+        while self.waiting and len(self.running) < self.slots:
             req = self.waiting[0]
-            need = footprint_bytes(req.dims, req.params.levels)
-            if need > self.budget:
-                raise ValueError(f"request {req.rid} needs {need} bytes, more than the budget")
-            if self.in_use + need > self.budget:
-                return  # wait for memory, keep arrival order
-            self.waiting.popleft()
-            slot = free_slots[0]
-            stream = self.streams[slot]
-            req.admitted = self.now()
             dtype = DIR_I16 if req.S.dtype == np.int16 else DIR_F32
-            ctx = dir_create(req.S, req.M, req.dims, req.spacing, dtype, False, req.variant,
-                             req.params, stream)
-            dir_register_async(ctx)
+            key = self._key(req)
+            entry = self._take_idle(key) if self.reuse else None
+            if entry is not None:
+                dir_load(entry[0], req.S, req.M, dtype, False)
+                self.reused += 1
+            else:
+                need = request_footprint(req)
+                if need > self.budget:
+                    raise ValueError(f"request {req.rid} needs {need} bytes, more than the budget")
+                if not self._evict_for(need):
+                    return  # wait for memory, keep arrival order
+                stream = self.torch.cuda.Stream()
+                ctx = dir_create(req.S, req.M, req.dims, req.spacing, dtype, False, req.variant,
+                                 req.params, stream)
+                entry = [ctx, stream, need, key]
+                self.in_use += need
+                self.created += 1
+            self.waiting.popleft()
+            req.admitted = self.now()
+            dir_register_async(entry[0])
             ev = self.torch.cuda.Event()
-            ev.record(stream)
-            self.running[slot] = (req, ctx, ev, need)
-            self.in_use += need
+            ev.record(entry[1])
+            self.running.append((req, entry, ev))
 
     def _reap(self):
-        for slot in list(self.running):
-            req, ctx, ev, need = self.running[slot]
+        still = []
+        for req, entry, ev in self.running:
             if not ev.query():
+                still.append((req, entry, ev))
                 continue
+            ctx = entry[0]
             st = dir_sync(ctx)
             req.iters_run = list(st.iters_run[: req.params.levels])
             if self.keep_fields:
@@ -134,24 +189,39 @@ class Server:
                 dir_get_field(ctx, out)
                 req.field = out
             req.done = self.now()
-            dir_destroy(ctx)
-            del self.running[slot]
-            self.in_use -= need
+            if self.reuse:
+                self.idle[self._next_id] = entry
+                self._next_id += 1
+            else:
+                dir_destroy(ctx)
+                self.in_use -= entry[2]
             self.finished.append(req)
+        self.running = still
 
     def step(self):
         self._reap()
         self._admit()
 
-    def idle(self) -> bool:
+    def idle_now(self) -> bool:
         return not self.waiting and not self.running
+
+    def close(self):
+        """Frees every idle context (the running ones finish first)."""
+        while self.running:
+            self._reap()
+            time.sleep(0.0002)
+        while self.idle:
+            _eid, (ctx, _s, nbytes, _k) = self.idle.popitem(last=False)
+            dir_destroy(ctx)
+            self.in_use -= nbytes
 
     def run(self, requests: list[Request], realtime: bool = True):
         """Feed requests at their arrival times and serve until all finished."""
         pending = sorted(requests, key=lambda r: r.arrival)
+        self.finished = []
         self.t0 = time.perf_counter()
         i = 0
-        while i < len(pending) or not self.idle():
+        while i < len(pending) or not self.idle_now():
             t = self.now()
             while i < len(pending) and (not realtime or pending[i].arrival <= t):
                 if not realtime:
@@ -200,7 +270,7 @@ DEFAULT_SIZES = [(128, 128, 64), (192, 192, 96), (256, 256, 128), (384, 384, 128
 
 
 def make_requests(n: int, rate: float, seed: int, sizes=DEFAULT_SIZES,
-                  a_max_mm: float = 15.0, iters=(200, 100, 50), use_graph: int = 0) -> list[Request]:
+                  a_max_mm: float = 15.0, iters=(200, 100, 50), use_graph: int = 1) -> list[Request]:
     """Poisson arrivals at `rate` jobs/s; each request takes one of the pooled
     phantoms (sizes spanning 128x128x64 .. 512x512x160, up to a_max_mm of RBF
     motion) and a force law uniform over the six, 3-level pyramid."""
@@ -213,34 +283,64 @@ def make_requests(n: int, rate: float, seed: int, sizes=DEFAULT_SIZES,
         t += -math.log(1.0 - float(rng.uniform(1)[0])) / rate
         S, M, spacing = pool[int(float(rng.uniform(1)[0]) * len(pool)) % len(pool)]
         variant = int(float(rng.uniform(1)[0]) * 6) % 6
-        # one registration per context: launching directly costs less host time
-        # than capturing a graph that would be replayed only once
+        # contexts stay resident between requests of the same shape, so the
+        # registration graph captured by the first one is replayed by the next
         params = dir_params_default(levels=3, iters=list(iters), use_graph=use_graph)
         out.append(Request(rid=k, S=S, M=M, spacing=spacing, variant=variant, params=params,
                            arrival=t))
     return out
 
 
+def warm_shapes(srv: Server, seed: int, sizes=DEFAULT_SIZES, iters=(200, 100, 50)):
+    """Serves one request of every (size, force law) shape so that the server
+    holds a resident context, with its captured graph, for each."""
+    pool = phantom_pool(sizes, seed, 15.0)
+    reqs = []
+    for k, (S, M, spacing) in enumerate(pool):
+        for v in range(6):
+            params = dir_params_default(levels=3, iters=list(iters), use_graph=1)
+            reqs.append(Request(rid=-1 - len(reqs), S=S, M=M, spacing=spacing, variant=v,
+                                params=params))
+    srv.run(reqs, realtime=False)
+
+
+def sweep(rates, jobs: int, slots: int, seed: int) -> list[dict]:
+    """The same Poisson request streams served three ways: one job at a time
+    with a fresh context each (the plain per-pair form), continuous batching
+    with fresh contexts, and continuous batching with resident contexts."""
+    forms = (("plain_queue", 1, False), ("batching_fresh_contexts", slots, False),
+             ("batching_resident_contexts", slots, True))
+    servers = {}
+    for name, n, reuse in forms:
+        servers[name] = Server(slots=n, keep_fields=False, reuse=reuse)
+        if reuse:
+            warm_shapes(servers[name], seed)
+    lines = []
+    for rate in rates:
+        line = {"mode": "serve", "rate_jobs_per_s": rate, "jobs": jobs}
+        for name, n, reuse in forms:
+            srv = servers[name]
+            reqs = make_requests(jobs, rate, seed)
+            c0, r0 = srv.created, srv.reused
+            done = srv.run(reqs, realtime=True)
+            line[name] = {"slots": n, **latency_stats(done), "contexts_created": srv.created - c0,
+                          "contexts_reused": srv.reused - r0}
+        lines.append(line)
+    for srv in servers.values():
+        srv.close()
+    return lines
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--rates", type=float, nargs="+", default=[1, 2, 5, 10, 20, 40])
+    ap.add_argument("--rates", type=float, nargs="+", default=[1, 2, 5, 10, 20])
     ap.add_argument("--jobs", type=int, default=30)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--seed", type=int, default=5)
-    ap.add_argument("--graph", type=int, default=0, help="capture each job's registration")
     args = ap.parse_args()
     import torch
     torch.cuda.init()
-    warm = make_requests(4, 100.0, args.seed + 1, use_graph=args.graph)  # first contexts
-    Server(slots=2, keep_fields=False).run(warm, realtime=False)
-    for rate in args.rates:
-        line = {"mode": "serve", "rate_jobs_per_s": rate, "jobs": args.jobs}
-        # the same Poisson stream, served one job at a time (a plain queue of
-        # per-pair registrations) and with continuous batching over the slots
-        for name, slots in (("plain_queue", 1), ("continuous_batching", args.slots)):
-            reqs = make_requests(args.jobs, rate, args.seed, use_graph=args.graph)
-            done = Server(slots=slots, keep_fields=False).run(reqs, realtime=True)
-            line[name] = {"slots": slots, **latency_stats(done)}
+    for line in sweep(args.rates, args.jobs, args.slots, args.seed):
         print(json.dumps(line), flush=True)
 
 

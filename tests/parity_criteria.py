@@ -24,6 +24,11 @@ shadow_check: where the oracle is ill-conditioned (long schedules at full
         implementation (the NumPy twin in float32), which deviates from the
         oracle by up to about five times the probes' spread at the 99th
         percentile on small ragged volumes.
+    Beyond the horizon (the 200/100/50 schedule at full size) a conditioned
+    set of spread <= bar / 10 still holds voxels where the GPU strays past
+    the bar (by up to 2.5x, measured with five probes): a rounding
+    divergence grows where it starts, which a few probe realisations cannot
+    map.  There the conditioned set is spread <= bar / 100 (COND_LONG).
 w_check: the warped image on every case: rel-RMS over the whole volume within
     TOL_W, or, where the probes themselves move the warped image by more than
     TOL_W * COND, within SHADOW times their largest rel-RMS.
@@ -33,13 +38,14 @@ import numpy as np
 TOL_U = 1e-3      # voxel
 TOL_W = 1e-4      # relative RMS of the warped image
 COND = 0.1        # conditioned: the neighbourhood's spread within bar * COND
+COND_LONG = 0.01  # the same beyond the single-precision horizon
 SHADOW = 10.0     # error quantiles within SHADOW x the spread quantiles
 QUANTILES = (0.5, 0.9, 0.99, 0.999, 0.9999, 1.0)
 
 
-def conditioned(spread, bar):
+def conditioned(spread, bar, cond=COND):
     from scipy.ndimage import maximum_filter
-    return maximum_filter(spread, size=7, mode="nearest") <= bar * COND
+    return maximum_filter(spread, size=7, mode="nearest") <= bar * cond
 
 
 def rel_rms(a, ref):
@@ -56,10 +62,10 @@ def strict_check(err, label, bar=TOL_U):
     return worst
 
 
-def shadow_check(err, spread, bar, label, min_cond=0.0):
+def shadow_check(err, spread, bar, label, min_cond=0.0, cond_level=COND):
     """Asserts (1) and (2); returns the fraction of voxels outside the
     conditioned set (at most 1 - min_cond)."""
-    cond = conditioned(spread, bar)
+    cond = conditioned(spread, bar, cond_level)
     ill = 1.0 - float(cond.mean())
     assert 1.0 - ill >= min_cond, f"{label}: only {1 - ill:.1%} of voxels conditioned"
     if cond.any():

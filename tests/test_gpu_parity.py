@@ -35,8 +35,8 @@ import collections
 
 import numpy as np
 import pytest
-from parity_criteria import (COND, TOL_U, TOL_W, conditioned, rel_rms, shadow_check,
-                             strict_check, w_check)
+from parity_criteria import (COND, COND_LONG, TOL_U, TOL_W, conditioned, rel_rms,
+                             shadow_check, strict_check, w_check)
 
 torch = pytest.importorskip("torch")
 
@@ -105,29 +105,31 @@ def probe(S, M, variant, levels, iters, ref, rel, seeds=None, alpha=0.4, sigma=1
     return Spread(spread, w_rel)
 
 
-def check32(oracle, S, M, g, ref, spread, label, min_cond=0.0):
+def check32(oracle, S, M, g, ref, spread, label, min_cond=0.0, cond_level=COND):
     """FP32 field against the oracle: the bar on the conditioned set, shadowing
     elsewhere, and the warped image on every case (see parity_criteria)."""
     if not isinstance(spread, Spread):
         spread = Spread(spread, 0.0)
     err = np.abs(g["u"].astype(np.float64) - ref["u"]).max(axis=0)
-    ill = shadow_check(err, spread.map, TOL_U, label + " FP32", min_cond)
-    cond = conditioned(spread.map, TOL_U)
-    rel, wbar = w_check(g["W"], oracle.warp(M, ref["u"]), label, spread.w_rel)
+    cond = conditioned(spread.map, TOL_U, cond_level)
+    ill = 1.0 - float(cond.mean())
+    rel = rel_rms(g["W"], oracle.warp(M, ref["u"]))
+    du = float(err[cond].max()) if cond.any() else 0.0
+    c10 = conditioned(spread.map, TOL_U, COND)
+    du10 = float(err[c10].max()) if c10.any() else 0.0
+    # the per-law row first, so that a failing case still reports it
+    print(f"TABLE | {label} | max {err.max():.2e} | q99 {np.quantile(err, 0.99):.1e} | "
+          f"> bar {int((err > TOL_U).sum())} | conditioned at bar*{cond_level:g} {1 - ill:.3%} "
+          f"(max there {du:.2e}) | at bar*{COND:g} {float(c10.mean()):.3%} (max there "
+          f"{du10:.2e}) | rel-RMS(W) {rel:.1e} | probes: max {spread.map.max():.2e} q99 "
+          f"{np.quantile(spread.map, 0.99):.1e} W {spread.w_rel:.1e}")
+    shadow_check(err, spread.map, TOL_U, label + " FP32", min_cond, cond_level)
+    w_check(g["W"], oracle.warp(M, ref["u"]), label, spread.w_rel)
     n = ref["stats"].shape[0]
     assert g["hist"].shape[0] == n
     if n and ill == 0.0:
         np.testing.assert_allclose(g["hist"][:, 0], ref["stats"][:, 0], rtol=1e-3, atol=1e-6)
         np.testing.assert_allclose(g["hist"][:, 1:], ref["stats"][:, 1:], rtol=2e-3, atol=1e-3)
-    du = float(err[cond].max()) if cond.any() else 0.0
-    print(f"{label}: FP32 max|du| {du:.2e} on conditioned voxels ({1 - ill:.3%}), "
-          f"{err.max():.2e} everywhere (q99 {np.quantile(err, 0.99):.1e}, "
-          f"{int((err > TOL_U).sum())} voxels > bar); oracle FP32 spread "
-          f"{spread.map.max():.2e} (q99 {np.quantile(spread.map, 0.99):.1e}, "
-          f"{int((spread.map > TOL_U).sum())} > bar); rel-RMS(W) {rel:.1e} (bar {wbar:.1e})")
-    print(f"TABLE | {label} | {err.max():.2e} | {np.quantile(err, 0.99):.1e} | "
-          f"{int((err > TOL_U).sum())} | {1 - ill:.3%} | {rel:.1e} | {wbar:.1e} | "
-          f"{spread.map.max():.2e} | {np.quantile(spread.map, 0.99):.1e}")
     return du, rel, ill
 
 
@@ -395,16 +397,32 @@ FULL_VARIANTS = [(0, 0.4), (1, 0.4), (2, 0.4), (3, 0.4), (4, 0.4), (4, 2.0), (5,
 FULL_SPACING = (0.9, 0.9, 2.5)
 
 # Schedules within the single-precision horizon of each force law on the
-# 256 x 256 x 100 phantom: the oracle's FP32 probes move its field by at most
-# TOL_U / 10 there (asserted below), so the production kernels are held to
-# the bar on every voxel.  The adjusted force with alpha = 0.4 amplifies
-# rounding fastest (its FP32 probes move the field by 0.1 voxel after 35
-# iterations of the coarsest level), hence its shorter pyramid schedule.
-STRICT_SCHEDULES = {
-    "1x10": (1, [10]),
-    "3x20/10/5": (3, [20, 10, 5]),
-}
-STRICT_CASES = [(v, a, name) for v, a in FULL_VARIANTS for name in STRICT_SCHEDULES]
+# 256 x 256 x 100 phantom.  The oracle's FP32 probes (its state stored in
+# single precision, a coherent 2^-24 nudge) move its field, at the worst voxel,
+# by (measured with the oracle alone):
+#                 1x5      1x10     1x20     3x10/5/3  3x20/10/5
+#   Eq. 1         4.0e-5   9.8e-5   2.2e-3   3.7e-4    8.8e-4
+#   Eq. 2         4.3e-6   5.8e-6   1.6e-5   3.1e-4    3.1e-4
+#   Eq. 3         2.7e-5   2.2e-4   4.5e-4   8.8e-4    2.3e-3
+#   Eq. 4         1.3e-5   8.5e-5   2.9e-3   1.4e-3    7.6e-3
+#   Eq. 5 a0.4    3.6e-5   1.4e-3   1.9e-2   1.9e-2    1.8e-1
+#   Eq. 5 a2.0    ...      3.4e-5   3.2e-5   1.1e-3    1.1e-3
+#   Eq. 6         ...      5.7e-6   8.5e-5   1.2e-3    2.5e-3
+# Tier 1 (spread <= TOL_U / 10, asserted): the production kernels meet the bar
+# on every voxel.  Tier 2, the pyramid (the coarse levels' errors reach the
+# finest level doubled per level): spread <= TOL_U / 2, asserted, and the bar
+# on every voxel all the same -- the GPU's single-precision rounding must not
+# stray further from the oracle than the probes do.
+STRICT_SCHEDULES = {"1x5": (1, [5]), "1x10": (1, [10]), "1x20": (1, [20]),
+                    "3x10/5/3": (3, [10, 5, 3])}
+STRICT_TIER = {"1x5": 1, "1x10": 1, "1x20": 1, "3x10/5/3": 2}
+STRICT_CASES = [(0, 0.4, "1x5"), (0, 0.4, "1x10"), (0, 0.4, "3x10/5/3"),
+                (1, 0.4, "1x5"), (1, 0.4, "1x10"), (1, 0.4, "1x20"), (1, 0.4, "3x10/5/3"),
+                (2, 0.4, "1x5"),
+                (3, 0.4, "1x5"), (3, 0.4, "1x10"),
+                (4, 0.4, "1x5"),
+                (4, 2.0, "1x5"), (4, 2.0, "1x10"), (4, 2.0, "1x20"),
+                (5, 0.4, "1x5"), (5, 0.4, "1x10"), (5, 0.4, "1x20")]
 
 
 @pytest.mark.parametrize("variant,alpha,sched", STRICT_CASES)
@@ -421,7 +439,8 @@ def test_full_size_every_voxel(dl, full_phantom, variant, alpha, sched):
                           threaded=True)
     spread = probe(S, M, variant, levels, iters, ref, F32_NOISE, alpha=alpha)
     label = f"full v{variant} a{alpha} {sched}"
-    assert spread.map.max() <= TOL_U * COND, (
+    room = TOL_U * COND if STRICT_TIER[sched] == 1 else TOL_U / 2
+    assert spread.map.max() <= room, (
         f"{label}: schedule beyond the single-precision horizon "
         f"(oracle FP32 spread {spread.map.max():.2e})")
     W_ref = oracle.warp(M, ref["u"])
@@ -453,7 +472,11 @@ def test_full_size_parity(dl, full_phantom, variant, alpha):
     S, M = full_phantom["S"], full_phantom["M"]
     sched = dict(levels=3, iters=[200, 100, 50], alpha=alpha)
     ref = oracle.register(S, M, variant=variant, threaded=True, **sched)
-    spread32 = probe(S, M, variant, ref=ref, rel=F32_NOISE, **sched)
+    # beyond the horizon each rounding pattern grows into its own deviation:
+    # five single-precision probes (state in float, coherent +-2^-24, two
+    # independent 2^-24 noises) map where rounding can move the field
+    spread32 = probe(S, M, variant, ref=ref, rel=F32_NOISE,
+                     seeds=(0, oracle.ROUND32, 1, 2), **sched)
     g64 = gpu_register(dl, S, M, variant, spacing=FULL_SPACING, fp64=True, **sched)
 
     # where FP64 is chaotic, its sensitivity map is the larger of the FP64
@@ -464,11 +487,12 @@ def test_full_size_parity(dl, full_phantom, variant, alpha):
 
     check64(g64, ref, f"full v{variant} a{alpha}", spread64)
     g = gpu_register(dl, S, M, variant, spacing=FULL_SPACING, **sched)
-    check32(oracle, S, M, g, ref, spread32, f"full v{variant} a{alpha}")
+    check32(oracle, S, M, g, ref, spread32, f"full v{variant} a{alpha}", cond_level=COND_LONG)
     if variant in (0, 1):
         # the default schedule: fused iterations on the small levels
         gf = gpu_register(dl, S, M, variant, spacing=FULL_SPACING, fuse=2, **sched)
-        check32(oracle, S, M, gf, ref, spread32, f"full v{variant} a{alpha} fused small levels")
+        check32(oracle, S, M, gf, ref, spread32, f"full v{variant} a{alpha} fused small levels",
+                cond_level=COND_LONG)
     # synthetic landmark accuracy (Sec. 3.2 evaluation): error well below motion
     lm, sp = full_phantom["landmarks"], full_phantom["spacing"]
     ue = np.stack([oracle.interp(g["u"][c].astype(np.float64), lm[:, 0], lm[:, 1], lm[:, 2])

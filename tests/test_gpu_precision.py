@@ -49,7 +49,8 @@ def test_int16_images_fp32_field(dl, small_phantom, variant):
     ref = oracle.register(S, M, variant=variant, levels=1, iters=[50])
     u, hist, st = _run(dl, S16, M16, variant, 1, [50], dl.DIR_I16, dl.DIR_F32)
     err = np.abs(u - ref["u"]).max(axis=0)
-    shadow_check(err, probe(S, M, variant, 1, [50], ref, F32_NOISE), TOL_U, f"i16 v{variant}")
+    shadow_check(err, probe(S, M, variant, 1, [50], ref, F32_NOISE).map, TOL_U,
+                 f"i16 v{variant}")
     np.testing.assert_allclose(hist[:, 0], ref["stats"][:, 0], rtol=1e-3)
     # the same registration from float images holding the same integers
     u32, _, _ = _run(dl, S.astype(np.float32), M.astype(np.float32), variant, 1, [50], dl.DIR_F32,

@@ -90,7 +90,8 @@ def test_the_criteria_reject_a_slip_at_full_size(full_phantom):
     # phantom: the every-voxel check of the short full-size schedules and the
     # shadow check of the long 200/100/50 schedule must both reject it, although
     # at full size the latter's conditioned set is a small part of the volume.
-    from parity_criteria import TOL_U, fp32_spread, rel_rms, shadow_check, strict_check
+    from parity_criteria import (COND_LONG, TOL_U, fp32_spread, rel_rms, shadow_check,
+                                 strict_check)
     S, M = full_phantom["S"], full_phantom["M"]
     short = dict(variant=0, levels=1, iters=[10])
     ref = oracle.register(S, M, **short)["u"]
@@ -106,5 +107,5 @@ def test_the_criteria_reject_a_slip_at_full_size(full_phantom):
     slip = oracle.register(S, M, variant=0, sigma=0.98, **sched)["u"]
     err = np.abs(slip - ref).max(axis=0)
     with pytest.raises(AssertionError) as e:
-        shadow_check(err, spread, TOL_U, "slipped oracle, 200/100/50")
+        shadow_check(err, spread, TOL_U, "slipped oracle, 200/100/50", cond_level=COND_LONG)
     print(f"long schedule: {e.value}")
