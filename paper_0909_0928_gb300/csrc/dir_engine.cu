@@ -12,8 +12,10 @@
 // by later registrations, so the hundreds of small coarse-level launches cost
 // one graph launch.  A device-side stop flag per level lets the captured graph
 // skip the remaining iterations of a level without a host round trip.
-// Images and fields live on the device as float (DIR_F32) or double (DIR_F64);
-// the same kernel templates serve both.
+// Images and fields live on the device as float (DIR_F32) or double (DIR_F64).
+// Single precision runs the TMA-tiled production kernels, or with
+// plain_kernels the plain-load kernels; double precision runs the plain-load
+// kernels in double.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
