@@ -57,13 +57,15 @@ def _lib(threaded: bool = False) -> C.CDLL:
         lib.or_force_arrays.argtypes = [C.c_int, C.c_double] + [_dp] * 8 + [_dp] * 3 + [C.c_int64]
         lib.or_iterate.restype = C.c_int
         lib.or_iterate.argtypes = ([C.c_int, C.c_double, C.c_double] + [_dp] * 6 + [_dp] * 3 +
-                                   [C.c_int, C.c_int, C.c_int, _dp, _dp])
+                                   [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp])
+        lib.or_correlation.restype = C.c_double
+        lib.or_correlation.argtypes = [_dp, _dp, C.c_int64]
         lib.or_ic_field.restype = None
         lib.or_ic_field.argtypes = [_dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]
         lib.or_register.restype = C.c_int
         lib.or_register.argtypes = ([_dp, _dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.c_double, C.c_int, _ip, C.c_int, C.c_double, C.c_int, _dp,
-                                     _dp, _dp, _ip, _dp, C.c_double, C.c_uint64])
+                                     _dp, _dp, _ip, _dp, C.c_double, C.c_uint64, _dp])
         lib.or_num_threads.restype = C.c_int
         lib.or_num_threads.argtypes = []
         _LIBS[threaded] = lib
@@ -172,8 +174,18 @@ def force(variant: int, d, gs, gm=None, b=None, alpha: float = 1.0) -> np.ndarra
     return out.reshape((3,) + d.shape)
 
 
-def iterate(variant: int, S, M, u, sigma: float = 1.0, alpha: float = 1.0):
-    """One iteration at one level.  Returns (new field, [sum d^2, sum|du|, sum|u|])."""
+def correlation(a, b) -> float:
+    """Pearson correlation coefficient of two images (NaN if one is constant)."""
+    a = _f64(a).ravel()
+    b = _f64(b).ravel()
+    if a.size != b.size:
+        raise ValueError("images of different sizes")
+    return float(_lib().or_correlation(_p(a), _p(b), a.size))
+
+
+def iterate(variant: int, S, M, u, sigma: float = 1.0, alpha: float = 1.0, corr: bool = False):
+    """One iteration at one level.  Returns (new field, [sum d^2, sum|du|, sum|u|]),
+    plus the correlation coefficient of the warped image(s) if corr."""
     S = _f64(S)
     M = _f64(M)
     u = _f64(u).copy()
@@ -184,12 +196,14 @@ def iterate(variant: int, S, M, u, sigma: float = 1.0, alpha: float = 1.0):
         bm = np.ascontiguousarray(np.sqrt(np.sum(grad(M) ** 2, axis=0)))
     work = np.empty((8,) + S.shape, dtype=np.float64)
     red = np.zeros(3, dtype=np.float64)
+    rho = np.zeros(1, dtype=np.float64)
     rc = _lib().or_iterate(int(variant), float(alpha), float(sigma), _p(S), _p(M), _p(gs[0]),
                            _p(gs[1]), _p(gs[2]), _p(bm) if bm is not None else None, _p(u[0]),
-                           _p(u[1]), _p(u[2]), nx, ny, nz, _p(work), _p(red))
+                           _p(u[1]), _p(u[2]), nx, ny, nz, _p(work), _p(red),
+                           _p(rho) if corr else None)
     if rc != 0:
         raise ValueError(f"or_iterate failed: {rc}")
-    return u, red
+    return (u, red, float(rho[0])) if corr else (u, red)
 
 
 def ic_field(h) -> np.ndarray:
@@ -207,11 +221,14 @@ ROUND32 = 0xFFFFFFFFFFFFFFFF  # probe_seed: single-precision storage of the stat
 def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: float = 1.0,
              alpha: float = 0.4, stop_mode: int = 0, eps: float = 1e-4, stop_window: int = 10,
              init=None, threaded: bool = True, return_raw: bool = False,
-             probe_rel: float = 0.0, probe_seed: int = 0):
+             probe_rel: float = 0.0, probe_seed: int = 0, return_corr: bool = False):
     """Whole registration.  `iters` lists iterations per level, coarsest first.
 
     Returns dict(u=(3, nz, ny, nx) field in voxels, stats=(n, 3) per-iteration
-    [MSE, sum|du|, sum|u|], iters_run=list per level[, raw=iterated field]).
+    [MSE, sum|du|, sum|u|], iters_run=list per level[, raw=iterated field]
+    [, corr=(n,) correlation coefficient of the warped image with S per
+    iteration, before its update (Eq. 6: of the two warped images)]).
+    stop_mode 2 stops a level on the correlation instead of the relative norm.
     probe_rel > 0 injects relative noise of that size into the warped images
     and the smoothed field every iteration (keyed by probe_seed): a probe of
     how strongly the iteration amplifies rounding, not part of the method.
@@ -228,16 +245,21 @@ def register(S, M, variant: int = PASSIVE, levels: int = 1, iters=(50,), sigma: 
     run = (C.c_int * 8)()
     u = np.empty((3,) + S.shape, dtype=np.float64)
     raw = np.empty_like(u) if return_raw else None
+    want_corr = return_corr or int(stop_mode) == 2
+    corr = np.full(max(total, 1), np.nan) if want_corr else None
     ini = _f64(init) if init is not None else None
     rc = _lib(threaded).or_register(_p(S), _p(M), nx, ny, nz, int(variant), float(alpha),
                                     float(sigma), int(levels), it, int(stop_mode), float(eps),
                                     int(stop_window), _p(ini) if ini is not None else None,
                                     _p(u), _p(stats), run, _p(raw) if raw is not None else None,
-                                    float(probe_rel), int(probe_seed) & 0xFFFFFFFFFFFFFFFF)
+                                    float(probe_rel), int(probe_seed) & 0xFFFFFFFFFFFFFFFF,
+                                    _p(corr) if corr is not None else None)
     if rc != 0:
         raise ValueError(f"or_register failed: {rc}")
     runs = [int(run[i]) for i in range(levels)]
     out = {"u": u, "stats": stats[: sum(runs)], "iters_run": runs}
     if return_raw:
         out["raw"] = raw
+    if want_corr:
+        out["corr"] = corr[: sum(runs)]
     return out

@@ -372,6 +372,33 @@ static void probe_perturb(double* a, size_t n, uint64_t which) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Pearson correlation coefficient of two images (the similarity measure the  */
+/* paper sets against its relative-norm stop test, Secs. 2.4 and 3.3):        */
+/*   rho = sum (a - mean a)(b - mean b) / sqrt(sum (a - mean a)^2 sum (b - mean b)^2) */
+/* in two passes (means, then centred sums).  NaN when either image is        */
+/* constant.                                                                  */
+/* ------------------------------------------------------------------------- */
+OR_EXPORT double or_correlation(const double* a, const double* b, int64_t n) {
+    if (n <= 0) return NAN;
+    double ma = 0.0, mb = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+        ma += a[c];
+        mb += b[c];
+    }
+    ma /= (double)n;
+    mb /= (double)n;
+    double sab = 0.0, saa = 0.0, sbb = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+        const double da = a[c] - ma, db = b[c] - mb;
+        sab += da * db;
+        saa += da * da;
+        sbb += db * db;
+    }
+    if (saa == 0.0 || sbb == 0.0) return NAN;
+    return sab / sqrt(saa * sbb);
+}
+
+/* ------------------------------------------------------------------------- */
 /* One demons iteration at one level (Fig. 1 flow: interpolation, gradient,   */
 /* displacement, low-pass filter, comparison).                                 */
 /*   S, M     static and moving image of the level                            */
@@ -380,12 +407,14 @@ static void probe_perturb(double* a, size_t n, uint64_t which) {
 /*   u*       field in/out (u for Eqs. 1-5; the mid-space field h for Eq. 6)  */
 /*   work     scratch of 8 * N doubles                                        */
 /*   red      out: [sum d^2, sum |du|, sum |u| before the update]            */
+/*   corr     NULL, or out: correlation coefficient of the warped moving image */
+/*            with S (Eq. 6: of the two warped images) before the update      */
 /* Returns 0, or a negative code on bad arguments.                            */
 /* ------------------------------------------------------------------------- */
 OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* S,
                          const double* M, const double* gsx, const double* gsy, const double* gsz,
                          const double* bm, double* ux, double* uy, double* uz, int nx, int ny,
-                         int nz, double* work, double red[3]) {
+                         int nz, double* work, double red[3], double* corr) {
     if (variant < 0 || variant > 5) return -1;
     size_t n = (size_t)nx * ny * nz;
     double* W = work;            /* warped moving image W_m */
@@ -407,6 +436,8 @@ OR_EXPORT int or_iterate(int variant, double alpha, double sigma, const double* 
     if (ic) probe_perturb(Ws, n, 2);
     probe_round(W, S, n);
     if (ic) probe_round(Ws, S, n);
+
+    if (corr) *corr = or_correlation(W, ic ? Ws : S, (int64_t)n);
 
     /* gradient of the deformed image(s), recomputed every iteration (Sec. 2.2) */
     if (uses_gm) {
@@ -504,7 +535,10 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /* Whole registration (Secs. 2.1-2.4).                                        */
 /*   levels       pyramid depth, 1 = single scale (the paper uses 2)          */
 /*   iters[l]     iterations at level l, l = 0 the COARSEST level             */
-/*   stop_mode    0 fixed counts; 1 relative-norm test of Sec. 2.4 per level  */
+/*   stop_mode    0 fixed counts; 1 relative-norm test of Sec. 2.4 per level; */
+/*                2 the same test on the correlation coefficient of the warped */
+/*                image with S (the criterion Sec. 2.4 argues against):       */
+/*                |rho(n) - rho(n - window)| <= eps                           */
 /*   init         NULL, or a level-0 field (3 planar arrays) to start from;   */
 /*                only with levels == 1                                       */
 /*   u_out        3 planar arrays of N doubles at full resolution, voxels     */
@@ -513,6 +547,9 @@ OR_EXPORT void or_ic_field(const double* hx, const double* hy, const double* hz,
 /*   iters_run    per level (coarsest first), iterations actually run         */
 /*   raw_out      NULL, or 3 planar arrays of N doubles that receive the      */
 /*                iterated field itself (h for Eq. 6, equal to u_out else)    */
+/*   corr_out     NULL, or per iteration run: the correlation coefficient of   */
+/*                the warped moving image with S before the update (Eq. 6: of */
+/*                the two warped images); needed (non-NULL) for stop_mode 2   */
 /*   probe_rel    0 normally.  > 0 turns on a conditioning probe that is not  */
 /*                part of the method: every iteration multiplies each warped  */
 /*                intensity and each smoothed field value by (1 + probe_rel * */
@@ -532,11 +569,12 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
                           int variant, double alpha, double sigma, int levels, const int* iters,
                           int stop_mode, double eps, int stop_window, const double* init,
                           double* u_out, double* stats, int* iters_run, double* raw_out,
-                          double probe_rel, uint64_t probe_seed) {
+                          double probe_rel, uint64_t probe_seed, double* corr_out) {
     if (variant < 0 || variant > 5 || levels < 1 || levels > OR_MAX_LEVELS) return -1;
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     if (init && levels != 1) return -1;
     if (stop_mode && stop_window < 1) return -1;
+    if (stop_mode < 0 || stop_mode > 2 || (stop_mode == 2 && !corr_out)) return -1;
 
     int dims[OR_MAX_LEVELS][3];
     double* Sl[OR_MAX_LEVELS] = {0};
@@ -628,7 +666,7 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
             probe_now.key = probe_seed * 0x9E3779B97F4A7C15ull + (uint64_t)stat_at + 1;
             rc = or_iterate(variant, alpha, sigma, Sl[l], Ml[l], gsx, gsy, gsz,
                             variant == OR_EVOLVED_PASSIVE ? bm : NULL, ux, uy, uz, cx, cy, cz,
-                            work, red);
+                            work, red, corr_out ? &corr_out[stat_at] : NULL);
             if (rc) break;
             stats[3 * stat_at + 0] = red[0] / (double)nl;
             stats[3 * stat_at + 1] = red[1];
@@ -638,8 +676,10 @@ OR_EXPORT int or_register(const double* S0, const double* M0, int nx, int ny, in
             lhist[stat_at] = red[2] > 0.0 ? red[1] / red[2] : NAN;
             ++stat_at;
             ++run;
-            /* Sec. 2.4 stop test, read as |l(n) - l(n - window)| <= eps within a level */
-            if (stop_mode == 1 && it >= stop_window) {
+            /* Sec. 2.4 stop test, read as |l(n) - l(n - window)| <= eps within a level;
+               stop_mode 2 applies it to the correlation coefficient instead */
+            if (stop_mode == 2) lhist[stat_at - 1] = corr_out[stat_at - 1];
+            if (stop_mode >= 1 && it >= stop_window) {
                 double ln = lhist[stat_at - 1];
                 double lp = lhist[level_start + it - stop_window];
                 if (!isnan(ln) && !isnan(lp) && fabs(ln - lp) <= eps) break;

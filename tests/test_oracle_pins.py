@@ -485,3 +485,55 @@ def test_two_iterations_are_local(variant):
     # and the margin matters: two voxels from an inner face the crop differs
     near = (slice(None),) + (slice(2, C - 2),) * 3
     assert np.abs(full[(slice(None),) + sl][near] - crop[near]).max() > 1e-3
+
+
+# ------------------------------------------------------ correlation coefficient
+
+def test_correlation_against_its_definition():
+    # Secs. 2.4 and 3.3: the Pearson correlation of two images, checked
+    # against numpy's corrcoef (an independent implementation) and its
+    # invariants
+    a = random_volume((9, 8, 7), seed=61) * 300 - 700
+    b = 0.4 * a + random_volume((9, 8, 7), seed=62) * 50
+    assert oracle.correlation(a, b) == pytest.approx(np.corrcoef(a.ravel(), b.ravel())[0, 1],
+                                                     abs=1e-13)
+    assert oracle.correlation(a, a) == pytest.approx(1.0, abs=1e-15)
+    assert oracle.correlation(a, -a) == pytest.approx(-1.0, abs=1e-15)
+    assert oracle.correlation(a, 3.0 * b + 11.0) == pytest.approx(oracle.correlation(a, b),
+                                                                   abs=1e-14)
+    assert math.isnan(oracle.correlation(a, np.full_like(a, 5.0)))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_iteration_correlation_is_that_of_the_warped_images(variant):
+    # the per-iteration correlation is taken on the pre-update warped image
+    # and S (Eq. 6: the two warped images M(x + h) and S(x - h))
+    S, M = make_blob_pair((14, 12, 10), (0.7, -0.4, 0.3), seed=9, n_blobs=12, sigma_vox=2.5)
+    u = np.stack([np.full(S.shape, 0.3), np.full(S.shape, -0.2), np.full(S.shape, 0.1)])
+    u[0] += random_volume(S.shape[::-1], seed=3) * 0.2
+    _, _, rho = oracle.iterate(variant, S, M, u, alpha=0.4, corr=True)
+    if variant == 5:
+        a, b = oracle.warp(M, u), oracle.warp(S, u, sign=-1.0)
+    else:
+        a, b = oracle.warp(M, u), S
+    assert rho == pytest.approx(np.corrcoef(a.ravel(), b.ravel())[0, 1], abs=1e-12)
+    _, _, one = oracle.iterate(variant, S, S.copy(), np.zeros_like(u), alpha=0.4, corr=True)
+    assert one == pytest.approx(1.0, abs=1e-14)
+
+
+def test_correlation_stop_test_property(small_phantom):
+    # stop_mode 2: a level stops at the first iteration n >= window with
+    # |rho(n) - rho(n - window)| <= eps, and not before
+    S, M = small_phantom["S"], small_phantom["M"]
+    eps, w = 2e-4, 5
+    r = oracle.register(S, M, variant=0, levels=1, iters=[200], stop_mode=2, eps=eps,
+                        stop_window=w)
+    rho = r["corr"]
+    n = r["iters_run"][0]
+    assert w < n < 200 and rho.shape[0] == n
+    for it in range(w, n - 1):
+        assert abs(rho[it] - rho[it - w]) > eps
+    assert abs(rho[n - 1] - rho[n - 1 - w]) <= eps
+    full = oracle.register(S, M, variant=0, levels=1, iters=[n], return_corr=True)
+    np.testing.assert_array_equal(full["corr"], rho)
+    np.testing.assert_array_equal(full["u"], r["u"])
