@@ -377,9 +377,11 @@ def landmark_error_mm(u_vox, landmarks, u_true_mm, spacing):
 def run_study(args):
     """Accuracy studies on the full-size phantom with its known deformation
     (Sec. 3.2 evaluation on synthetic landmarks): every force law, the alpha
-    of Eq. (5) from 0.1 to 5, the relative-norm stop test of Sec. 2.4, and the
-    finest level iteration by iteration, each with the correlation of the
-    deformed moving image with S beside the landmark error (Sec. 3.3)."""
+    of Eq. (5) from 0.1 to 5, the relative-norm stop test of Sec. 2.4 and the
+    same test on the correlation coefficient (reduced on the device every
+    iteration), and the finest level iteration by iteration, each with the
+    correlation of the deformed moving image with S beside the landmark error
+    (Sec. 3.3)."""
     import numpy as np
     import torch
     import paper_0909_0928_gb300 as dl
@@ -403,9 +405,11 @@ def run_study(args):
         b = W.astype(np.float64) - W.mean()
         return float((a * b).sum() / np.sqrt((a * a).sum() * (b * b).sum()))
 
-    def run(variant, alpha=0.4, stop_mode=0, eps=1e-4, iters=ITERS, reps=3):
+    def run(variant, alpha=0.4, stop_mode=0, eps=1e-4, iters=ITERS, reps=3, curve=False):
+        # correlation = 1: the device reduces the correlation coefficient of the
+        # warped image with S every iteration, in the force pass
         p = dl.dir_params_default(levels=LEVELS, iters=list(iters), alpha=alpha,
-                                  stop_mode=stop_mode, eps=eps, stop_window=10)
+                                  stop_mode=stop_mode, eps=eps, stop_window=10, correlation=1)
         ctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, variant, p, stream)
         try:
             st = dl.dir_register(ctx)
@@ -414,20 +418,36 @@ def run_study(args):
             dl.dir_get_field(ctx, u)
             W = np.empty(ph["S"].shape, np.float32)
             dl.dir_warp(ctx, ph["M"], W)
+            rho = dl.dir_get_correlation(ctx, sum(iters))
+            hist = dl.dir_get_history(ctx, sum(iters))
         finally:
             dl.dir_destroy(ctx)
         m, sd = landmark_error_mm(u, lm, ut, SPACING)
-        return {"landmark_mm": {"mean": m, "sd": sd}, "ms": statistics.median(ms) if ms else None,
-                "iters_run": list(st.iters_run[:LEVELS]), "mse_final": st.mse_final,
-                "relnorm_final": st.relnorm_final, "correlation": correlation(W)}
+        runs = list(st.iters_run[:LEVELS])
+        fine = slice(sum(runs[:-1]), sum(runs))
+        out = {"landmark_mm": {"mean": m, "sd": sd}, "ms": statistics.median(ms) if ms else None,
+               "iters_run": runs, "mse_final": st.mse_final, "relnorm_final": st.relnorm_final,
+               "correlation": correlation(W),
+               "correlation_device_last": float(rho[-1]) if rho.size else None}
+        if curve:  # the finest level, iteration by iteration (Fig. 3a)
+            h = hist[fine]
+            out["finest_curve"] = {
+                "correlation": [round(float(r), 6) for r in rho[fine]],
+                "relative_norm": [round(float(a / b), 6) if b > 0 else None for a, b in
+                                  zip(h[:, 1], h[:, 2])]}
+        return out
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    out["variants"] = {VARIANT_NAMES[v]: run(v) for v in range(6)}
+    out["variants"] = {VARIANT_NAMES[v]: run(v, curve=(v == 0)) for v in range(6)}
     out["alpha_sweep_adjusted_double"] = {str(a): run(4, alpha=a)
                                           for a in (0.1, 0.2, 0.4, 0.5, 1.0, 2.0, 3.0, 5.0)}
     out["stop_test_passive"] = {f"{e:g}": run(0, stop_mode=1, eps=e)
                                 for e in (1e-2, 1e-3, 1e-4, 1e-5)}
+    # the similarity criterion Sec. 2.4 argues against: the same windowed test
+    # on the correlation coefficient, decided on the device
+    out["stop_test_correlation_passive"] = {f"{e:g}": run(0, stop_mode=2, eps=e)
+                                            for e in (1e-3, 1e-4, 1e-5, 1e-6)}
     # the finest level iteration by iteration (Fig. 3a): a registration stopped
     # after k finest iterations is the state of iteration k of a longer one
     out["finest_iterations_passive"] = {

@@ -79,7 +79,11 @@ typedef struct {
                                     the filter radius is ceil(3 sigma), at most 8 */
     double alpha;                /* Eq. (5) normalisation factor (default 0.4) */
     int stop_mode;               /* 0: run iters exactly; 1: also stop a level when
-                                    |l(n) - l(n - stop_window)| <= eps (Sec. 2.4) */
+                                    |l(n) - l(n - stop_window)| <= eps (Sec. 2.4), l(n) the
+                                    relative norm; 2: the same test on the correlation
+                                    coefficient of the warped image with S (the similarity
+                                    criterion Sec. 2.4 sets against the relative norm; implies
+                                    correlation = 1) */
     double eps;                  /* default 1e-4 (Sec. 2.4) */
     int stop_window;             /* default 10 (Sec. 2.4) */
     dir_dtype field_dtype;       /* storage of the displacement field on the device: DIR_F32
@@ -113,6 +117,11 @@ typedef struct {
                                     memory, 32 x 8 smoothing tiles, never fused -- in single
                                     precision: a reference for the tiling, halo and ring code
                                     of the production kernels.  Slower; not for production. */
+    int correlation;             /* 1: record, every iteration, the correlation coefficient of
+                                    the warped moving image with S before the update (Eq. 6:
+                                    of the two warped images) with reductions fused into the
+                                    force pass (Secs. 2.4, 3.3; dir_get_correlation); 0
+                                    (default): not recorded */
 } dir_params;
 
 typedef struct {
@@ -210,6 +219,20 @@ int dir_get_field_f64(dir_ctx* ctx, double* out, int in_mm, int out_on_device);
  * host array out and returns that count, or a negative error.
  */
 int dir_get_history(dir_ctx* ctx, double* out, int max_iters);
+
+/*
+ * The correlation coefficient of the warped moving image with S (Eq. 6: of the
+ * two warped images) at every iteration of the last registration, before the
+ * update, in the order run (coarsest level first): the similarity measure that
+ * Sec. 2.4 contrasts with the relative norm and Sec. 3.3 (Fig. 3) plots
+ * against the iterations.  Its sums are reduced on the device in the force
+ * pass (FP32 within a block, FP64 across blocks); the quotient is formed here.
+ * Writes min(max_iters, iterations run) values (NaN where an image is
+ * constant) to the host array out and returns that count; DIR_EUNSUPPORTED
+ * unless the context was created with correlation = 1 or stop_mode = 2,
+ * DIR_ESTATE before the first registration.
+ */
+int dir_get_correlation(dir_ctx* ctx, double* out, int max_iters);
 
 /*
  * Warps an image on the static grid's dims by the registered field, with the

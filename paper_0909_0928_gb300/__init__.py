@@ -8,7 +8,7 @@ importing this package raises.
 
 Functions carry the C names: dir_params_default, dir_create, dir_load,
 dir_register, dir_register_async, dir_sync, dir_get_field, dir_get_field_f64,
-dir_get_history, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version,
+dir_get_history, dir_get_correlation, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version,
 dir_register_noalloc, dir_batch_create, dir_batch_run, dir_batch_destroy,
 dir_autotune, dir_check_wait_timeout.
 `Registration` wraps a context for convenience.
@@ -34,7 +34,8 @@ VARIANTS = {"passive": 0, "evolved_passive": 1, "active": 2, "double": 3, "adjus
 
 # every symbol the C header declares
 EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_register_async",
-           "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history", "dir_warp", "dir_destroy",
+           "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history",
+           "dir_get_correlation", "dir_warp", "dir_destroy",
            "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc",
            "dir_batch_create", "dir_batch_run", "dir_batch_destroy", "dir_autotune",
            "dir_check_wait_timeout"]
@@ -45,7 +46,8 @@ class DirParams(C.Structure):
                 ("alpha", C.c_double), ("stop_mode", C.c_int), ("eps", C.c_double),
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
                 ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
-                ("precision", C.c_int), ("fuse", C.c_int), ("plain_kernels", C.c_int)]
+                ("precision", C.c_int), ("fuse", C.c_int), ("plain_kernels", C.c_int),
+                ("correlation", C.c_int)]
 
 
 class DirStats(C.Structure):
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_get_field": (ip, [vp, vp, ip, ip]),
         "dir_get_field_f64": (ip, [vp, vp, ip, ip]),
         "dir_get_history": (ip, [vp, C.POINTER(C.c_double), ip]),
+        "dir_get_correlation": (ip, [vp, C.POINTER(C.c_double), ip]),
         "dir_warp": (ip, [vp, vp, vp, ip, ip]),
         "dir_destroy": (None, [vp]),
         "dir_status_string": (C.c_char_p, [ip]),
@@ -259,6 +262,15 @@ def dir_get_history(ctx, max_iters: int) -> np.ndarray:
     return buf[:n]
 
 
+def dir_get_correlation(ctx, max_iters: int) -> np.ndarray:
+    """Per-iteration correlation coefficient of the warped image with S
+    (contexts created with correlation = 1 or stop_mode = 2)."""
+    buf = np.zeros(max(int(max_iters), 0), dtype=np.float64)
+    n = _check(_lib.dir_get_correlation(ctx, buf.ctypes.data_as(C.POINTER(C.c_double)),
+                                        int(max_iters)), "dir_get_correlation", ctx)
+    return buf[:n]
+
+
 def dir_warp(ctx, img_in, img_out, dtype=DIR_F32, on_device=False):
     _check(_lib.dir_warp(ctx, _ptr(img_in, on_device), _ptr(img_out, on_device), int(dtype),
                          int(bool(on_device))), "dir_warp", ctx)
@@ -365,6 +377,9 @@ class Registration:
 
     def history(self) -> np.ndarray:
         return dir_get_history(self.ctx, sum(self.params.iters[: self.params.levels]))
+
+    def correlation(self) -> np.ndarray:
+        return dir_get_correlation(self.ctx, sum(self.params.iters[: self.params.levels]))
 
     def warp(self, img, out=None):
         on_dev = _is_torch(img) and bool(img.is_cuda)

@@ -198,6 +198,51 @@ __device__ __forceinline__ void block_reduce3_atomic(Real a, Real b, Real c, dou
     }
 }
 
+// The sums of the correlation coefficient of the warped image with its
+// reference (Secs. 2.4, 3.3): per voxel b (S; Eq. 6: the warped static image)
+// and d = W - b; the field's own statistics keep Sum d^2.  Accumulated per
+// thread, then reduced like block_reduce3_atomic into out[0..3] =
+// {Sum b, Sum b^2, Sum d, Sum b d}.
+template <typename Real>
+struct CorrSums {
+    Real b = 0, bb = 0, d = 0, bd = 0;
+    __device__ __forceinline__ void add(Real bv, Real dv) {
+        b += bv;
+        bb = r_fma(bv, bv, bb);
+        d += dv;
+        bd = r_fma(bv, dv, bd);
+    }
+};
+
+template <int NT, typename Real>
+__device__ __forceinline__ void block_reduce4_atomic(const CorrSums<Real>& s, double* out) {
+    static_assert(NT % 32 == 0, "block size must be whole warps");
+    __shared__ double red4_s[4][NT / 32];
+    Real v[4] = {s.b, s.bb, s.d, s.bd};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red4_s[k][warp] = (double)v[k];
+    __syncthreads();
+    if (warp == 0) {
+        double dv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dv[k] = lane < NT / 32 ? red4_s[k][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dv[k] += __shfl_down_sync(0xffffffffu, dv[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(out + k, dv[k]);
+    }
+}
+
 // ------------------------------------------------- packed single precision
 // Two float lanes in one 64-bit register (low lane = first float in memory),
 // operated on by the f32x2 instructions of sm_100 and later: one instruction

@@ -130,6 +130,7 @@ struct dir_ctx {
     char* A = nullptr;
     char* B = nullptr;
     double* red = nullptr;
+    double* corr = nullptr;   // 4 sums per iteration of the correlation coefficient, or null
     double* lhist = nullptr;
     int* ctl = nullptr;
     int* derr = nullptr;
@@ -152,6 +153,7 @@ struct dir_ctx {
     int launches = 0;
     dirk::Taps taps, taps1;
     std::vector<double> red_host;
+    std::vector<double> corr_host;
     std::vector<int> ctl_host;
     int iters_run[DIR_MAX_LEVELS];
     std::string err;
@@ -244,6 +246,10 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
     const bool f64 = c->fp64;
     const bool plain = c->p.plain_kernels != 0;
     CK(c, cudaMemsetAsync(c->red, 0, sizeof(double) * 3 * (size_t)(c->total_iters > 0 ? c->total_iters : 1), s));
+    if (c->corr)
+        CK(c, cudaMemsetAsync(c->corr, 0,
+                              sizeof(double) * 4 * (size_t)(c->total_iters > 0 ? c->total_iters : 1),
+                              s));
     CK(c, cudaMemsetAsync(c->ctl, 0x7f, sizeof(int) * (size_t)L, s));
     CK(c, cudaMemsetAsync(c->derr, 0, sizeof(int), s));
 
@@ -338,6 +344,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     fa.u = cur;
                     fa.v = vbuf;
                     fa.red = c->red + 3 * (size_t)row;
+                    fa.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
                     fa.iter = it;
                     CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
                 } else {
@@ -352,6 +359,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     ua.stop_iter = c->ctl + lc;
                     ua.iter = it;
                     ua.err = c->derr;
+                    ua.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
                     CK(c, dirk::launch_fused(c->variant, f64, ua, c->num_sms, s));
                     char* t = vbuf;
                     vbuf = spare;
@@ -384,12 +392,16 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             fa.u = cur;
             fa.v = oth;
             fa.red = c->red + 3 * (size_t)row;
+            fa.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
             fa.iter = it;
             CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
             c->launches += 1;
-            if (c->p.stop_mode == 1) {
-                CK(c, dirk::launch_stop_test(c->red, c->lhist, row, c->level_first[lc],
-                                             c->p.stop_window, c->p.eps, c->ctl + lc, it, s));
+            if (c->p.stop_mode >= 1) {
+                // Sec. 2.4 on the relative norm, or (stop_mode 2) on the correlation
+                CK(c, dirk::launch_stop_test(c->red, c->p.stop_mode == 2 ? c->corr : nullptr,
+                                             (double)g.nx * g.ny * g.nz, c->lhist, row,
+                                             c->level_first[lc], c->p.stop_window, c->p.eps,
+                                             c->ctl + lc, it, s));
                 c->launches += 1;
             }
             if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -446,7 +458,7 @@ static void release(dir_ctx* c) {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap) cudaStreamDestroy(c->cap);
-    void* bufs[] = {c->img_pool, c->A, c->B, c->red, c->lhist, c->ctl, c->derr,
+    void* bufs[] = {c->img_pool, c->A, c->B, c->red, c->corr, c->lhist, c->ctl, c->derr,
                     c->stage_img, c->stage_f32, c->stage_f64};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
@@ -460,8 +472,9 @@ static int validate_params(const dir_params* p) {
     dirk::Taps t;
     if (!make_taps(p->sigma, &t)) return DIR_EINVAL;
     if (!isfinite(p->alpha)) return DIR_EINVAL;
-    if (p->stop_mode != 0 && p->stop_mode != 1) return DIR_EINVAL;
-    if (p->stop_mode == 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
+    if (p->stop_mode < 0 || p->stop_mode > 2) return DIR_EINVAL;
+    if (p->stop_mode >= 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
+    if (p->correlation != 0 && p->correlation != 1) return DIR_EINVAL;
     if (p->precision != DIR_F32 && p->precision != DIR_F64) return DIR_EUNSUPPORTED;
     if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
@@ -507,6 +520,7 @@ int dir_params_default(dir_params* p) {
     p->precision = DIR_F32;
     p->fuse = 2;
     p->plain_kernels = 0;
+    p->correlation = 0;
     return DIR_OK;
 }
 
@@ -609,6 +623,8 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         cudaMallocAsync(&c->A, field * c->fesz, st) != cudaSuccess ||
         cudaMallocAsync(&c->B, field * c->fesz, st) != cudaSuccess ||
         cudaMallocAsync(&c->red, 3 * nred * sizeof(double), st) != cudaSuccess ||
+        ((p.correlation || p.stop_mode == 2) &&
+         cudaMallocAsync(&c->corr, 4 * nred * sizeof(double), st) != cudaSuccess) ||
         cudaMallocAsync(&c->lhist, nred * sizeof(double), st) != cudaSuccess ||
         cudaMallocAsync(&c->ctl, DIR_MAX_LEVELS * sizeof(int), st) != cudaSuccess ||
         cudaMallocAsync(&c->derr, sizeof(int), st) != cudaSuccess) {
@@ -695,6 +711,11 @@ int dir_sync(dir_ctx* c, dir_stats* st) {
     c->ctl_host.resize(DIR_MAX_LEVELS + 1);
     CK(c, cudaMemcpyAsync(c->red_host.data(), c->red, 3 * nred * sizeof(double),
                           cudaMemcpyDeviceToHost, c->stream));
+    if (c->corr) {
+        c->corr_host.resize(4 * nred);
+        CK(c, cudaMemcpyAsync(c->corr_host.data(), c->corr, 4 * nred * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+    }
     CK(c, cudaMemcpyAsync(c->ctl_host.data(), c->ctl, c->levels * sizeof(int),
                           cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(c->ctl_host.data() + DIR_MAX_LEVELS, c->derr, sizeof(int),
@@ -776,6 +797,22 @@ int dir_get_history(dir_ctx* c, double* out, int max_iters) {
             out[3 * w + 0] = r[0] / n;
             out[3 * w + 1] = r[1];
             out[3 * w + 2] = r[2];
+        }
+    }
+    return w;
+}
+
+int dir_get_correlation(dir_ctx* c, double* out, int max_iters) {
+    if (!c || (!out && max_iters > 0) || max_iters < 0) return DIR_EINVAL;
+    if (!c->corr) return DIR_EUNSUPPORTED;  // not asked for at dir_create
+    if (!c->have_field) return DIR_ESTATE;
+    int w = 0;
+    for (int lc = 0; lc < c->levels; ++lc) {
+        const Grid3& g = c->lv[c->levels - 1 - lc].g;
+        const double n = (double)g.nx * g.ny * g.nz;
+        for (int it = 0; it < c->iters_run[lc] && w < max_iters; ++it, ++w) {
+            const size_t row = (size_t)(c->level_first[lc] + it);
+            out[w] = dirk::correlation_from_sums(c->red_host[3 * row], &c->corr_host[4 * row], n);
         }
     }
     return w;
@@ -1234,6 +1271,9 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
     at = align256(at + field * c.fesz);
     const size_t offRed = at;
     at = align256(at + 3 * nred * sizeof(double));
+    const bool want_corr = p.correlation || p.stop_mode == 2;
+    const size_t offCorr = at;
+    if (want_corr) at = align256(at + 4 * nred * sizeof(double));
     const size_t offL = at;
     at = align256(at + nred * sizeof(double));
     const size_t offCtl = at;
@@ -1284,6 +1324,7 @@ extern "C" int dir_register_noalloc(const float* static_img, const float* moving
     c.A = base + offA;
     c.B = base + offB;
     c.red = reinterpret_cast<double*>(base + offRed);
+    c.corr = want_corr ? reinterpret_cast<double*>(base + offCorr) : nullptr;
     c.lhist = reinterpret_cast<double*>(base + offL);
     c.ctl = reinterpret_cast<int*>(base + offCtl);
     c.derr = reinterpret_cast<int*>(base + offErr);

@@ -206,6 +206,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
     }
 
     Real sd2 = 0, sdu = 0, su = 0;  // per-thread partial sums
+    CorrSums<Real> corr_s;          // with a.corr: the correlation sums
     if (col_valid) {
 #pragma unroll
         for (int k = 0; k < FTZ; ++k) {
@@ -241,6 +242,11 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
                 } else {
                     d = interp_rel(M, ip, x, ux, y, uy, z, uz, scol[k + 1]);
                 }
+                if (a.corr) {  // reference: S (Eq. 6: the warped static image S + D_s)
+                    Real bref = scol[k + 1];
+                    if constexpr (T::IC) bref += Real(0.5) * (Wt[k + 1][ty + 1][tx + 1] - d);
+                    corr_s.add(bref, d);
+                }
                 Real dx, dy, dz;
                 demons_force<Real, V>(d, gsx, gsy, gsz, gmx, gmy, gmz, bm, alpha2, dx, dy, dz);
                 dx = -dx;
@@ -256,6 +262,7 @@ __global__ void __launch_bounds__(FNT, 4) force_kernel(const ForceArgs a) {
         }
     }
     block_reduce3_atomic<FNT, Real>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<FNT, Real>(corr_s, a.corr);
 }
 
 template <typename Real, typename TI, typename TF, int FTZ>

@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(FNT, 4)
     const Interp ip(g);
     const int cs = (int)g.cs;
     float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    CorrSums<float> corr_s;  // with a.corr: the correlation sums
     if (col_valid) {
 #pragma unroll
         for (int k = 0; k < FTZ; ++k) {
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(FNT, 4)
                     bm = r_sqrt(mx * mx + my * my + mz * mz);
                 }
                 const float d = interp_rel(M, ip, x, ux, y, uy, z, uz, s0);  // W - S
+                if (a.corr) corr_s.add(s0, d);
                 float dx, dy, dz;
                 demons_force<float, V>(d, gsx, gsy, gsz, 0.0f, 0.0f, 0.0f, bm, 0.0f, dx, dy, dz);
                 dx = -dx;
@@ -151,6 +153,7 @@ __global__ void __launch_bounds__(FNT, 4)
         }
     }
     block_reduce3_atomic<FNT, float>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<FNT, float>(corr_s, a.corr);
 }
 
 template <typename TI>
@@ -334,6 +337,7 @@ __global__ void __launch_bounds__(FNT, 4)
     const int sy = yc - sy0, sym = max(yc - 1, 0) - sy0, syp = min(yc + 1, g.ny - 1) - sy0;
     const int cs = (int)g.cs;
     float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    CorrSums<float> corr_s;  // with a.corr: the correlation sums
     if (col_valid) {
 #pragma unroll
         for (int k = 0; k < FTZ; ++k) {
@@ -355,6 +359,11 @@ __global__ void __launch_bounds__(FNT, 4)
                 const float gmy = r_fma(ns, gsy, 0.5f * (W1[HX] - W1[-HX]));
                 const float gmz = r_fma(ns, gsz, 0.5f * (dcol[k + 2] - dcol[k]));
                 const float d = dd[k];
+                if (a.corr) {  // reference: S (Eq. 6: the warped static image S + D_s)
+                    float bref = (float)Sc[sy * FSW + sx];
+                    if (F::IC) bref += 0.5f * (dcol[k + 1] - d);
+                    corr_s.add(bref, d);
+                }
                 const int ui = (((k + 1) * UH) + (ty + 1)) * UW + (tx + 4);
                 const float ux = ub[ui], uy = ub[ui + UC], uz = ub[ui + 2 * UC];
                 float dx, dy, dz;
@@ -373,6 +382,7 @@ __global__ void __launch_bounds__(FNT, 4)
         }
     }
     block_reduce3_atomic<FNT, float>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<FNT, float>(corr_s, a.corr);
 }
 
 template <typename TI>

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
         m_0 = __ldg(M + offs(g, xc, yc, z0));
     }
     Real sd2 = 0, sdu = 0, su = 0;  // per-thread partial sums
+    CorrSums<Real> corr_s;          // with a.corr: the correlation sums
 
     for (int step = 0; step < pipe.nsteps; ++step) {
         if (!pipe.template xpass<FUSED_NT>(&tmap, g, step, tid, w, a.err)) {
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
                 const Real uy = utile[(1 * STY + fy) * STX + fx];
                 const Real uz = utile[(2 * STY + fy) * STX + fx];
                 const Real d = trilinear(M, g, x, ux, y, uy, zo, uz, s_0);  // W - S
+                if (a.corr) corr_s.add(s_0, d);
                 const int ro = offs(g, 0, y, zo);
                 const Real gsx = Real(0.5) * (__ldg(S + ro + xp) - __ldg(S + ro + xm));
                 const Real gsy =
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(FUSED_NT, R <= 4 ? 2 : 1)
         }
     }
     block_reduce3_atomic<FUSED_NT, Real>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<FUSED_NT, Real>(corr_s, a.corr);
 }
 
 template <typename Real, int R, int V>
@@ -292,6 +295,7 @@ __global__ void __launch_bounds__(F2T, 2)
     const Interp ip(g);
     const int cs = (int)g.cs;
     float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    CorrSums<float> corr_s;  // with a.corr: the correlation sums
 
     for (int step = 0; step < nsteps; ++step) {
         if (tid == 0 && step + F2ST - 1 < nsteps) issue(step + F2ST - 1);
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(F2T, 2)
                     const float gsy = 0.5f * (Sc[syp * F2SW + sxc] - Sc[sym * F2SW + sxc]);
                     const float gsz = 0.5f * (Sp[syc * F2SW + sxc] - Sm[syc * F2SW + sxc]);
                     const float d = interp_rel(M, ip, x, ux, y, uy, zo, uz, s0);  // W - S
+                    if (a.corr) corr_s.add(s0, d);
                     float bm = 0.0f;
                     if (V == 1) {
                         const int o = offs(g, x, y, zo);
@@ -380,6 +385,7 @@ __global__ void __launch_bounds__(F2T, 2)
         // of the S ring before they are rewritten
     }
     block_reduce3_atomic<F2T, float>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<F2T, float>(corr_s, a.corr);
 }
 
 template <int R>
@@ -565,6 +571,7 @@ __global__ void __launch_bounds__(F2T, 1)
     const int cs = (int)g.cs;
     const int spa = max(0, -zs), spb = min(F::SNP - 1, g.nz - 1 - zs);  // in-volume S planes
     float sd2 = 0.0f, sdu = 0.0f, su = 0.0f;
+    CorrSums<float> corr_s;  // with a.corr: the correlation sums
     for (int k = tid; k < FZC * S2Y * S2X; k += F2T) {
         const int j = k / (S2Y * S2X), row = (k / S2X) % S2Y, fx = k % S2X;
         const int x = x0 + fx, y = y0 + row, zo = z0 + j;
@@ -581,6 +588,7 @@ __global__ void __launch_bounds__(F2T, 1)
         const float gsy = 0.5f * (Sc[syp * F2SW + sxc] - Sc[sym * F2SW + sxc]);
         const float gsz = 0.5f * (Sp[syc * F2SW + sxc] - Sm[syc * F2SW + sxc]);
         const float d = interp_rel(M, ip, x, ux, y, uy, zo, uz, s0);  // W - S
+        if (a.corr) corr_s.add(s0, d);
         float bm = 0.0f;
         if (V == 1) {
             const int o = offs(g, x, y, zo);
@@ -606,6 +614,7 @@ __global__ void __launch_bounds__(F2T, 1)
         vout[o + 2 * cs] = uz + dz;
     }
     block_reduce3_atomic<F2T, float>(sd2, sdu, su, a.red);
+    if (a.corr) block_reduce4_atomic<F2T, float>(corr_s, a.corr);
 }
 
 // one block per SM with FZC-plane chunks covers the level

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include "dir_common.cuh"
 
@@ -32,6 +33,8 @@ struct ForceArgs {
     int pf_stride = 0;   // > 0: each block prefetches into L2 the brick of the block
                          // this many linear indices ahead
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
+    double* corr = nullptr;  // non-null: += {Sum b, Sum b^2, Sum d, Sum b d} of the
+                             // correlation of the warped image with its reference
 };
 // plain = true: the plain-load force_kernel even where a TMA-fed kernel exists
 // (the same per-voxel arithmetic without the tiling; a cross-check of it)
@@ -72,6 +75,7 @@ struct FusedArgs {
     const int* stop_iter;
     int iter;
     int* err;
+    double* corr = nullptr;  // as ForceArgs::corr
 };
 bool fused_supported(int variant);
 // the level is small enough for the all-planes-at-once fused kernel (one block
@@ -103,8 +107,18 @@ cudaError_t launch_import(bool fp64, int out_type, const float* dense, void* pit
 // one bounded wait on an mbarrier that never completes; sets kErrTmaTimeout
 // in *err when it gives up after limit_ns
 cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_t s);
-// relative-norm stop test of Sec. 2.4 for iteration t of a level
-cudaError_t launch_stop_test(const double* red, double* lhist, int t, int level_first, int window,
-                             double eps, int* stop_iter, int iter_in_level, cudaStream_t s);
+// stop test of Sec. 2.4 for iteration t of a level on the relative norm
+// (corr == nullptr) or on the correlation coefficient of the warped image with
+// its reference (corr: the four sums of each iteration, n: voxels of the level)
+cudaError_t launch_stop_test(const double* red, const double* corr, double n, double* lhist,
+                             int t, int level_first, int window, double eps, int* stop_iter,
+                             int iter_in_level, cudaStream_t s);
+// correlation coefficient from Sum d^2 and the four sums of CorrSums over n voxels
+__host__ __device__ inline double correlation_from_sums(double sdd, const double* c, double n) {
+    const double sb = c[0], sbb = c[1], sd = c[2], sbd = c[3];
+    const double sa = sb + sd, saa = sbb + 2.0 * sbd + sdd, sab = sbb + sbd;
+    const double cov = sab - sa * sb / n, va = saa - sa * sa / n, vb = sbb - sb * sb / n;
+    return (va > 0.0 && vb > 0.0) ? cov / sqrt(va * vb) : nan("");
+}
 
 }  // namespace dirk

@@ -108,12 +108,13 @@ __global__ void import_kernel(const float* __restrict__ dense, TF* __restrict__ 
 
 // Sec. 2.4: l(t) = sum|du| / sum|u|; stop the level after iteration t when
 // |l(t) - l(t - window)| <= eps (both defined).  One thread.
-__global__ void stop_test_kernel(const double* __restrict__ red, double* lhist, int t,
-                                 int level_first, int window, double eps, int* stop_iter,
-                                 int iter_in_level) {
+__global__ void stop_test_kernel(const double* __restrict__ red, const double* __restrict__ corr,
+                                 double n, double* lhist, int t, int level_first, int window,
+                                 double eps, int* stop_iter, int iter_in_level) {
     if (*stop_iter < iter_in_level) return;
     const double B = red[3 * t + 2];
-    const double l = B > 0.0 ? red[3 * t + 1] / B : nan("");
+    const double l = corr ? correlation_from_sums(red[3 * t], corr + 4 * t, n)
+                          : (B > 0.0 ? red[3 * t + 1] / B : nan(""));
     lhist[t] = l;
     if (iter_in_level >= window && t - window >= level_first) {
         const double lp = lhist[t - window];
@@ -214,9 +215,10 @@ cudaError_t launch_wait_probe(int* err, unsigned long long limit_ns, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_stop_test(const double* red, double* lhist, int t, int level_first, int window,
-                             double eps, int* stop_iter, int iter_in_level, cudaStream_t s) {
-    stop_test_kernel<<<1, 1, 0, s>>>(red, lhist, t, level_first, window, eps, stop_iter,
+cudaError_t launch_stop_test(const double* red, const double* corr, double n, double* lhist,
+                             int t, int level_first, int window, double eps, int* stop_iter,
+                             int iter_in_level, cudaStream_t s) {
+    stop_test_kernel<<<1, 1, 0, s>>>(red, corr, n, lhist, t, level_first, window, eps, stop_iter,
                                      iter_in_level);
     return cudaGetLastError();
 }

@@ -621,3 +621,76 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable(dl, small_phantom):
     assert dl.dir_check_wait_timeout(stream, 0.0) == dl.DIR_EINVAL
     after = gpu_register(dl, S, M, 0, 2, [5, 5])
     assert np.array_equal(before["u"], after["u"])
+
+
+# ------------------------------------------------------- correlation coefficient
+
+@pytest.mark.parametrize("variant,fuse,plain", [(0, 0, 0), (0, 1, 0), (1, 1, 0), (2, 0, 0),
+                                                (5, 0, 0), (5, 0, 1), (3, 0, 1)])
+def test_correlation_matches_the_oracle(dl, small_phantom, variant, fuse, plain):
+    # Secs. 2.4, 3.3: the correlation coefficient of the warped image with S
+    # (Eq. 6: of the two warped images) every iteration, reduced on the device
+    # in the force pass, against the oracle's; the production, fused and plain
+    # kernels alike
+    import oracle
+    S, M = small_phantom["S"], small_phantom["M"]
+    sched = dict(levels=2, iters=[12, 20])
+    ref = oracle.register(S, M, variant=variant, alpha=0.4, return_corr=True, **sched)
+    params = dl.dir_params_default(alpha=0.4, correlation=1, fuse=fuse, plain_kernels=plain,
+                                   **sched)
+    with dl.Registration(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (1, 1, 2.5),
+                         variant, params, torch.cuda.current_stream()) as reg:
+        reg.register()
+        rho = reg.correlation()
+        u = reg.field()
+    assert rho.shape == ref["corr"].shape
+    err = float(np.abs(rho - ref["corr"]).max())
+    print(f"correlation v{variant} fuse {fuse} plain {plain}: max |drho| {err:.2e} "
+          f"(rho {rho[0]:.5f} .. {rho[-1]:.5f})")
+    assert err <= 1e-5
+    # the sums only observe: the field is the one of the same registration
+    # without them, bit for bit (the field's own parity is covered above)
+    params0 = dl.dir_params_default(alpha=0.4, correlation=0, fuse=fuse, plain_kernels=plain,
+                                    **sched)
+    with dl.Registration(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (1, 1, 2.5),
+                         variant, params0, torch.cuda.current_stream()) as reg:
+        reg.register()
+        u0 = reg.field()
+    assert np.array_equal(u, u0)
+
+
+def test_correlation_stop_test_on_the_device(dl, small_phantom):
+    # stop_mode 2: the level stops at the first iteration n >= window whose
+    # correlation moved by at most eps over the window, decided on the device
+    # inside the captured graph
+    import oracle
+    S, M = small_phantom["S"], small_phantom["M"]
+    eps, w = 2e-4, 5
+    params = dl.dir_params_default(levels=1, iters=[200], stop_mode=2, eps=eps, stop_window=w)
+    with dl.Registration(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (1, 1, 2.5), 0,
+                         params, torch.cuda.current_stream()) as reg:
+        st = reg.register()
+        rho = reg.correlation()
+        u = reg.field()
+    n = st.iters_run[0]
+    assert w < n < 200 and rho.shape[0] == n
+    for it in range(w, n - 1):
+        assert abs(rho[it] - rho[it - w]) > eps * (1 - 1e-9)
+    assert abs(rho[n - 1] - rho[n - 1 - w]) <= eps * (1 + 1e-9)
+    ref = oracle.register(S, M, variant=0, levels=1, iters=[200], stop_mode=2, eps=eps,
+                          stop_window=w)
+    # the stop iteration is an FP decision; when both stop at the same
+    # iteration the fields must agree to the bar
+    if ref["iters_run"][0] == n:
+        assert np.abs(u - ref["u"]).max() <= TOL_U
+    print(f"correlation stop: device {n}, oracle {ref['iters_run'][0]} iterations")
+
+
+def test_correlation_needs_to_be_asked_for(dl, small_phantom):
+    S, M = small_phantom["S"], small_phantom["M"]
+    params = dl.dir_params_default(levels=1, iters=[3])
+    with dl.Registration(S, M, (1, 1, 2.5), 0, params) as reg:
+        reg.register()
+        with pytest.raises(dl.DirError) as e:
+            reg.correlation()
+        assert e.value.code == dl.DIR_EUNSUPPORTED
