@@ -108,6 +108,9 @@ KERNEL_SOURCES = {
                       "dir_force_law.cuh", "dir_common.cuh"],
     "fused_small_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
                            "dir_force_law.cuh", "dir_common.cuh"],
+    "smooth_xy_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
+    "force_zs_kernel": ["dir_force_zs.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
+                        "dir_stencil.cuh", "dir_common.cuh"],
 }
 
 
@@ -546,9 +549,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "batch", "study", "precision", "serve"])
-    ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2],
-                    help="fold the Gaussian into the next force pass (Eqs. 1-2): 0 never, "
-                         "1 every level, 2 (library default) the small levels")
+    ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2, 3],
+                    help="iteration schedule for Eqs. 1-2: 0 force + smoothing kernels, 1 fused, "
+                         "3 split Gaussian (x/y kernel, z pass inside the force kernel), "
+                         "2 the library default (split where it applies)")
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
     if args.warmup < 3:
@@ -629,9 +633,11 @@ def main():
     tctx = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, args.variant_id, tparams,
                          stream)
     kt = {"force": [0.0, 0], "fused": [0.0, 0], "smooth": [0.0, 0]}
+    schedule = 0
     for i in range(args.warmup + max(3, min(args.steps, 10))):
         flush.zero_()
         st = dl.dir_register(tctx)
+        schedule = st.schedule_finest
         if i < args.warmup:
             continue
         for k, ms, n in (("force", st.ms_force_finest, st.n_force_finest),
@@ -674,6 +680,8 @@ def main():
                 "smooth": SMOOTH_BYTES}
     kernel_of = {"force": "force_tma_kernel" if args.variant_id in (0, 1) else "force_tma_gm_kernel",
                  "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
+    if schedule == 2:  # split Gaussian: x/y kernel, then z pass + force (same bytes per voxel)
+        kernel_of.update(force="force_zs_kernel", smooth="smooth_xy_kernel")
     per_kernel = {}
     for k, (ms, n) in kt.items():
         if n:
@@ -703,10 +711,11 @@ def main():
     per_variant = None
     if not args.no_variants:
         per_variant = {}
-        # the library's default schedule (fuse = 2) for every force law, plus
-        # passive with the two-kernel schedule everywhere (0) and fused everywhere (1)
-        for vid, alpha, fuse in ((0, 0.4, 2), (0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 2), (2, 0.4, 2),
-                                 (3, 0.4, 2), (4, 0.4, 2), (4, 2.0, 2), (5, 0.4, 2)):
+        # the library's default schedule (fuse = 2: the split Gaussian for
+        # Eqs. 1-2) for every force law, plus Eqs. 1-2 with the two-kernel
+        # schedule everywhere (0) and passive fused everywhere (1)
+        for vid, alpha, fuse in ((0, 0.4, 2), (0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 2), (1, 0.4, 0),
+                                 (2, 0.4, 2), (3, 0.4, 2), (4, 0.4, 2), (4, 2.0, 2), (5, 0.4, 2)):
             p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, fuse=fuse)
             c2 = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, vid, p2, stream)
             ms = []
@@ -717,7 +726,7 @@ def main():
                     ms.append(st.ms_total)
             dl.dir_destroy(c2)
             name = VARIANT_NAMES[vid] + (f"_alpha{alpha}" if vid == 4 else "") + \
-                {2: "", 0: "_two_kernel", 1: "_fused_all_levels"}[fuse]
+                {2: "", 0: "_two_kernel", 1: "_fused_all_levels", 3: "_split_gaussian"}[fuse]
             med = statistics.median(ms)
             per_variant[name] = {"ms_p50": med, "voxel_updates_per_s": vu_step / (med / 1e3)}
 

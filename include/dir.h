@@ -104,12 +104,18 @@ typedef struct {
                                     precision for verification against an FP64 reference; it
                                     runs the plain-load kernels of plain_kernels = 1 in double,
                                     not the TMA-tiled single-precision kernels) */
-    int fuse;                    /* for Eqs. (1)-(2) without the stop test, with FP32 images and
-                                    field: fold the Gaussian of iteration k into the force pass of
-                                    iteration k+1 (same arithmetic, one pass over the field per
-                                    iteration).  0: never; 1: every level; 2 (default): the small
-                                    levels that one block per SM covers in two-plane chunks
-                                    (e.g. 64 x 64 x 25), where it is faster */
+    int fuse;                    /* iteration schedule for Eqs. (1)-(2) (the same field bit for bit
+                                    in every schedule; Eqs. (3)-(6) always run force + smoothing).
+                                    0: a force kernel, then a smoothing kernel.  1: fused -- the
+                                    Gaussian of iteration k folded into the force pass of
+                                    iteration k+1 (FP32 images and field, no stop test), every
+                                    level.  3: split -- the Gaussian's x and y passes as their own
+                                    kernel plane by plane, its z pass inside the force kernel down
+                                    each thread's z column (FP32 field, float or int16 images,
+                                    sigma with radius 3, any stop_mode), every level.  2
+                                    (default): split where it applies, else fused on the small
+                                    levels that one block per SM covers in two-plane chunks (e.g.
+                                    64 x 64 x 25), else 0 */
     int plain_kernels;           /* 0 (default): the production kernels (TMA-fed bricks and
                                     plane rings, packed smoothing, fused small levels).  1: the
                                     plain-load kernels with the same per-voxel arithmetic and
@@ -141,6 +147,10 @@ typedef struct {
     int kernel_launches;            /* kernels launched by the registration (incl. early exits) */
     float ms_fused_finest;          /* with params.timing: summed fused-iteration time at level 0, ms */
     int n_fused_finest;             /* number of launches behind ms_fused_finest */
+    int schedule_finest;            /* iteration schedule of level 0: 0 force + smoothing kernels,
+                                       1 fused iteration, 2 split Gaussian (fuse = 3); with the
+                                       split schedule ms_smooth_finest times the x/y kernel and
+                                       ms_force_finest the z + force kernel */
 } dir_stats;
 
 /* Fills *p with the defaults listed above.  Returns DIR_EINVAL if p is NULL. */
@@ -265,7 +275,8 @@ void dir_batch_destroy(dir_batch* batch);  /* NULL-safe */
 /*
  * Launch-shape autotuning for one context, after a finished dir_register:
  * for each pyramid level, times the force kernel with 1, 2, 4 and 8 voxels
- * per thread along z and the smoothing kernel with several z chunks
+ * per thread along z and the smoothing kernel with several z chunks (on
+ * levels of the split schedule, the z + force kernel and the x/y kernel)
  * (`reps` launches each), keeps the fastest of each for the context's later
  * registrations (and batches built afterwards), and writes them to
  * shapes_out[2*l], shapes_out[2*l+1] for level l (finest = 0) if not NULL.

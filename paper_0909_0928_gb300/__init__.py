@@ -57,7 +57,8 @@ class DirStats(C.Structure):
                 ("ms_force_finest", C.c_float), ("ms_smooth_finest", C.c_float),
                 ("n_force_finest", C.c_int), ("n_smooth_finest", C.c_int),
                 ("voxel_updates", C.c_longlong), ("kernel_launches", C.c_int),
-                ("ms_fused_finest", C.c_float), ("n_fused_finest", C.c_int)]
+                ("ms_fused_finest", C.c_float), ("n_fused_finest", C.c_int),
+                ("schedule_finest", C.c_int)]
 
     def as_dict(self) -> dict:
         return {"levels": self.levels, "iters_run": list(self.iters_run[: self.levels]),
@@ -67,7 +68,8 @@ class DirStats(C.Structure):
                 "ms_smooth_finest": self.ms_smooth_finest,
                 "n_force_finest": self.n_force_finest, "n_smooth_finest": self.n_smooth_finest,
                 "voxel_updates": self.voxel_updates, "kernel_launches": self.kernel_launches,
-                "ms_fused_finest": self.ms_fused_finest, "n_fused_finest": self.n_fused_finest}
+                "ms_fused_finest": self.ms_fused_finest, "n_fused_finest": self.n_fused_finest,
+                "schedule_finest": self.schedule_finest}
 
 
 class DirError(RuntimeError):

@@ -138,7 +138,8 @@ struct dir_ctx {
     int level_first[DIR_MAX_LEVELS];
     int fused_level[DIR_MAX_LEVELS];
     int tune_depth[DIR_MAX_LEVELS] = {0};    // force brick depth per level, 0 = heuristic
-    int tune_zchunk[DIR_MAX_LEVELS] = {0};   // smoothing z chunk per level, 0 = one wave
+    int tune_zchunk[DIR_MAX_LEVELS] = {0};   // smoothing z chunk per level (of the x/y kernel
+                                             // on split levels), 0 = the launcher's choice
     char* final_field = nullptr;
     bool have_field = false;
     bool pending = false;
@@ -240,6 +241,31 @@ static int record(dir_ctx* c, cudaEvent_t e, cudaStream_t s, bool capturing) {
 }
 
 // Issues the whole registration on stream s (captured or direct).
+// Iteration schedule of pyramid level l: 0 force + smoothing kernels, 1 fused
+// iteration (the Gaussian of v_{k-1} folded into the force pass), 2 split
+// Gaussian (its x and y passes as their own kernel, its z pass inside the
+// force kernel).  All three give the same field bit for bit.  fuse = 2 (the
+// default) takes the split schedule where it applies (Eqs. 1-2, FP32 field,
+// radius 3) and otherwise the fused one on the small levels: measured on the
+// 256x256x100 pyramid, the split schedule is fastest on every level.
+static int level_schedule(const dir_ctx* c, int l) {
+    if (c->fp64 || c->p.plain_kernels) return 0;
+    const Grid3& g = c->lv[l].g;
+    const bool split_ok = c->field_type == dirk::kStoreF32 && (c->variant == 0 || c->variant == 1) &&
+                          (c->img_type(l) == dirk::kStoreF32 || c->img_type(l) == dirk::kStoreI16) &&
+                          c->taps.R == 3;
+    const bool fused_ok = c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
+                          c->field_type == c->real_type && c->img_type(l) == c->real_type;
+    switch (c->p.fuse) {
+        case 1: return fused_ok ? 1 : 0;
+        case 2:
+            if (split_ok) return 2;
+            return fused_ok && dirk::fused_small_level(g, c->num_sms) ? 1 : 0;
+        case 3: return split_ok ? 2 : 0;
+        default: return 0;
+    }
+}
+
 static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
     c->launches = 0;
     const int L = c->levels;
@@ -324,15 +350,8 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
         sa.zchunk = c->tune_zchunk[l];
         const bool timed = c->p.timing && l == 0;
         const int n = c->p.iters[lc];
-        // fuse = 2: only the small levels, where the fused iteration's single
-        // copy per block beats two launches; on larger levels the two-kernel
-        // schedule keeps more blocks in flight (measured on 256x256x100)
-        const bool fuse_here =
-            c->p.fuse == 1 || (c->p.fuse == 2 && dirk::fused_small_level(g, c->num_sms));
-        const bool fused = fuse_here && !plain && c->p.stop_mode == 0 &&
-                           dirk::fused_supported(c->variant) &&
-                           c->field_type == c->real_type && c->img_type(l) == c->real_type;
-        if (fused && n > 0) {
+        const int sched = level_schedule(c, l);
+        if (sched == 1 && n > 0) {
             // iteration 0 from u, iterations 1..n-1 from the previous v with the
             // smoothing folded in, then one smoothing of the last v
             char* vbuf = oth;
@@ -383,6 +402,57 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                 if (timed) c->n_timed += 1;
             }
             c->fused_level[lc] = 1;
+            continue;
+        }
+        if (sched == 2 && n > 0) {
+            // iteration 0 from u; iteration k > 0: t = G_y G_x v (xy kernel), then
+            // v = u - dr(u) with u = G_z t (force kernel); then u = G v of the last
+            // iteration run
+            char* vbuf = oth;
+            char* tbuf = cur;
+            dirk::SmoothArgs xa = sa;
+            xa.in = vbuf;
+            xa.out = tbuf;
+            xa.zchunk = c->tune_zchunk[l];  // 0: the launcher's own chunking
+            for (int it = 0; it < n; ++it, ++row) {
+                cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
+                if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
+                fa.red = c->red + 3 * (size_t)row;
+                fa.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
+                fa.iter = it;
+                fa.v = vbuf;
+                if (it == 0) {
+                    fa.u = cur;
+                    CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
+                    c->launches += 1;
+                    if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
+                } else {
+                    xa.iter = it;
+                    CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s));
+                    if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
+                    fa.u = tbuf;
+                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
+                    c->launches += 2;
+                }
+                if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
+                if (c->p.stop_mode >= 1) {
+                    CK(c, dirk::launch_stop_test(c->red, c->p.stop_mode == 2 ? c->corr : nullptr,
+                                                 (double)g.nx * g.ny * g.nz, c->lhist, row,
+                                                 c->level_first[lc], c->p.stop_window, c->p.eps,
+                                                 c->ctl + lc, it, s));
+                    c->launches += 1;
+                }
+                if (timed) c->n_timed += 1;
+            }
+            sa.in = vbuf;
+            sa.out = tbuf;
+            sa.iter = 0;
+            sa.stop_iter = nullptr;  // always: v of the last iteration run
+            CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
+            c->launches += 1;
+            cur = tbuf;
+            oth = vbuf;
+            c->fused_level[lc] = 2;
             continue;
         }
         c->fused_level[lc] = 0;
@@ -479,7 +549,7 @@ static int validate_params(const dir_params* p) {
     if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
-    if (p->fuse < 0 || p->fuse > 2) return DIR_EINVAL;
+    if (p->fuse < 0 || p->fuse > 3) return DIR_EINVAL;
     if (p->plain_kernels != 0 && p->plain_kernels != 1) return DIR_EINVAL;
     return DIR_OK;
 }
@@ -755,13 +825,24 @@ int dir_sync(dir_ctx* c, dir_stats* st) {
         st->ms_total = ms;
         st->voxel_updates = vu;
         st->kernel_launches = c->launches;
+        st->schedule_finest = c->fused_level[fin];
         if (c->p.timing) {
             const int runs = c->iters_run[fin];
-            const bool fused = c->fused_level[fin] != 0;
+            const bool fused = c->fused_level[fin] == 1;
+            const bool split = c->fused_level[fin] == 2;
             for (int i = 0; i < c->n_timed && i < runs; ++i) {
                 float a = 0.f, b = 0.f;
                 CK(c, cudaEventElapsedTime(&a, c->tev[3 * i], c->tev[3 * i + 1]));
                 CK(c, cudaEventElapsedTime(&b, c->tev[3 * i + 1], c->tev[3 * i + 2]));
+                if (split) {  // iterations > 0: the xy smoothing, then the z + force kernel
+                    if (i > 0) {
+                        st->ms_smooth_finest += a;
+                        st->n_smooth_finest += 1;
+                        st->ms_force_finest += b;
+                        st->n_force_finest += 1;
+                    }
+                    continue;
+                }
                 if (fused && i > 0) {
                     st->ms_fused_finest += a;
                     st->n_fused_finest += 1;
@@ -1127,12 +1208,14 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         fa.field_type = c->field_type;
         fa.err = c->derr;
         fa.pf_stride = c->num_sms;  // as in the registration
+        const bool split = level_schedule(c, l) == 2;  // time the kernels the level runs
         float best = 1e30f;
         int best_d = 0;
         for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {
             fa.depth = d;
             float ms = 0.0f;
             rc = timed([&]() {
+                if (split) return dirk::launch_force_zs(c->variant, fa, c->taps, c->stream);
                 return dirk::launch_force(c->variant, c->fp64, fa, c->stream, c->p.plain_kernels != 0);
             }, &ms);
             if (rc == DIR_OK && ms < best) {
@@ -1161,6 +1244,7 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
             sa.zchunk = cand[k];
             float ms = 0.0f;
             rc = timed([&]() {
+                if (split) return dirk::launch_smooth_xy(sa, c->num_sms, c->stream);
                 return dirk::launch_smooth(c->fp64, sa, c->num_sms, c->stream, c->p.plain_kernels != 0);
             }, &ms);
             if (rc == DIR_OK && ms < best) {

@@ -35,15 +35,6 @@ struct FTGeom {
     static constexpr int SMEM = 128 + OFF_BAR + 64;
 };
 
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2,
-                                                int c3) {
-    asm volatile(
-        "cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-            reinterpret_cast<uint64_t>(map)),
-        "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
-
 template <int V, int FTZ, typename TI>
 __global__ void __launch_bounds__(FNT, 4)
     force_tma_kernel(const __grid_constant__ CUtensorMap umap,

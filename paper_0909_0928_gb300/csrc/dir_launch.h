@@ -62,6 +62,19 @@ struct SmoothArgs {
 cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStream_t s,
                           bool plain = false);
 
+// The x and y passes of the Gaussian alone, plane by plane (single precision,
+// three components, radius 1..4): out = G_y * G_x * in.  With
+// launch_force_zs, which applies G_z, one smoothing + force iteration.
+bool smooth_xy_supported(const SmoothArgs& a);
+cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
+
+// Force pass of Eqs. 1-2 whose u is G_z * t, t = a.u the output of
+// launch_smooth_xy (single-precision field, float or int16 images, radius 3):
+// v = u - dr(u) and the reductions of ForceArgs, the same field bit for bit as
+// launch_smooth + launch_force.  Brick depth a.depth (8, 4, 2 or 1).
+bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
+cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
+
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
 // force kernel's work, v = u - dr(u); red as for ForceArgs.
 struct FusedArgs {

@@ -179,6 +179,100 @@ __global__ void __launch_bounds__(8 * TY, 16 / TY * 8)
 }
 
 // ---------------------------------------------------------------------------
+// The x and y passes alone (single precision, three components), for the
+// schedule that runs the z pass inside the force kernel (dir_force_tma.cu):
+// out(x, y, z) = G_y * G_x * in on every plane, plane by plane.  Without a z
+// pass there is no z halo, so a block's z chunk can be as short as the
+// occupancy wants at no extra work, and there is no ring of filtered planes.
+// Same building blocks, layout and order of operations as smooth2_kernel.
+// ---------------------------------------------------------------------------
+constexpr int SXYSTAGES = 4;
+
+template <int R, int TY>
+struct SXYSmem {
+    using G = S2Geom<R, TY>;
+    static constexpr int SMEM = 128 + SXYSTAGES * G::SLOT_STRIDE + G::TXP_STRIDE + 64;
+};
+
+template <int R, int TY>
+__global__ void __launch_bounds__(8 * TY)
+    smooth_xy_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
+    using G = S2Geom<R, TY>;
+    constexpr int H = G::H, HA = G::HA, WB = G::WB, NT = G::NTG;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    f32x2* txp = reinterpret_cast<f32x2*>(base + SXYSTAGES * G::SLOT_STRIDE);
+    float* txf = reinterpret_cast<float*>(txp);
+    uint64_t* full =
+        reinterpret_cast<uint64_t*>(base + SXYSTAGES * G::SLOT_STRIDE + G::TXP_STRIDE);
+    const Grid3 g = a.g;
+    float w[R + 1];
+    f32x2 wp[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) {
+        w[t] = a.taps.wf[t];
+        wp[t] = f2_pack(w[t], w[t]);
+    }
+    const int tid = threadIdx.x;
+    const int lx = tid & 31, q = tid >> 5;
+    const int comp = blockIdx.z % a.ncomp;
+    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * TY;
+    const int z0 = (blockIdx.z / a.ncomp) * zchunk;
+    const int nsteps = min(z0 + zchunk, g.nz) - z0;  // planes z0 .. z0 + nsteps - 1
+    const int bx = x0 - HA, by = y0 - R;
+    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
+    float* __restrict__ out = static_cast<float*>(a.out) + (long long)comp * g.cs;
+
+    auto issue = [&](int step) {
+        const int sl = step % SXYSTAGES;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
+        tma_load_4d(base + sl * G::SLOT_STRIDE, &tmap, bx, by, z0 + step, comp, &full[sl]);
+    };
+    if (tid == 0) {
+        for (int sl = 0; sl < SXYSTAGES; ++sl) mbar_init(&full[sl], 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        for (int st = 0; st < SXYSTAGES - 1 && st < nsteps; ++st) issue(st);
+    }
+    __syncthreads();
+
+    const int x = x0 + lx;
+    const int ya = y0 + 2 * q;  // rows ya, ya + 1 (lane 0) and ya + TY/2, ya + TY/2 + 1 (lane 1)
+    const int px = (int)g.px;
+    const int rows_left = x < g.nx ? g.ny - ya : 0;  // 0: this thread stores nothing
+    for (int step = 0; step < nsteps; ++step) {
+        if (tid == 0 && step + SXYSTAGES - 1 < nsteps) issue(step + SXYSTAGES - 1);
+        const int sl = step % SXYSTAGES;
+        const uint32_t parity = (uint32_t)((step / SXYSTAGES) & 1);
+        bool ok = true;
+        if (tid == 0) ok = mbar_wait_bounded(&full[sl], parity, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+            return;
+        }
+        (void)mbar_try_wait(&full[sl], parity);
+        float* slot = reinterpret_cast<float*>(base + sl * G::SLOT_STRIDE);  // [H][WB]
+        if (edge) s2_edge_fix<R, TY>(slot, G::SLOT_STRIDE / 4, 1, bx, by, g, tid, NT);
+        s2_xpass<R, TY>(slot, txf, tid, w);
+        __syncthreads();
+        f32x2 r0, r1;
+        s2_y_pair<R>(txp, q, lx, wp, r0, r1);
+        float a0, b0, a1, b1;
+        f2_unpack(r0, a0, b0);
+        f2_unpack(r1, a1, b1);
+        float* o = out + offs(g, x < g.nx ? x : 0, ya, z0 + step);
+        if (rows_left > 0) o[0] = a0;
+        if (rows_left > 1) o[px] = a1;
+        if (rows_left > TY / 2) o[(TY / 2) * px] = b0;
+        if (rows_left > TY / 2 + 1) o[(TY / 2 + 1) * px] = b1;
+        // the next step's __syncthreads_or orders this step's reads of the
+        // pair rows before the next x pass rewrites them
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Field smoothing for small levels: a block of 384 threads (a group of 128
 // per component) owns a 32 x 16 tile and SZC = 2 output planes, fetches the
 // SZC + 2R input planes of all three components in one TMA copy and runs the
@@ -380,6 +474,37 @@ static cudaError_t launch_s2t(const SmoothArgs& a, int num_sms, cudaStream_t s) 
     return launch_s2<R, S2Y>(a, num_sms, s);
 }
 
+template <int R, int TY>
+static cudaError_t launch_sxy(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    using G = SXYSmem<R, TY>;
+    CUtensorMap map;
+    if (!make_s2_map<R, TY>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
+    static KernelSetup setup;  // per instantiation
+    int per_sm = 1;
+    const cudaError_t e = setup_kernel(setup, smooth_xy_kernel<R, TY>, G::SMEM, 8 * TY, &per_sm);
+    if (e != cudaSuccess) return e;
+    // No z halo, so short chunks cost nothing extra: the longest of 4, 2, 1
+    // planes that still gives a wave of resident blocks (the autotuner's choice
+    // on each level of the 256x256x100 pyramid)
+    int zc = a.zchunk;
+    if (zc <= 0) {
+        const long long bxy =
+            (long long)((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + TY - 1) / TY) * a.ncomp;
+        const long long slots = (long long)(per_sm < 1 ? 1 : per_sm) * num_sms;
+        zc = 1;
+        for (int c = 4; c > 1; c /= 2)
+            if (bxy * ((a.g.nz + c - 1) / c) >= slots) {
+                zc = c;
+                break;
+            }
+    }
+    if (zc > a.g.nz) zc = a.g.nz;
+    const int chunks = (a.g.nz + zc - 1) / zc;
+    const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + TY - 1) / TY, chunks * a.ncomp);
+    smooth_xy_kernel<R, TY><<<grid, dim3(8 * TY, 1, 1), G::SMEM, s>>>(map, a, zc);
+    return cudaGetLastError();
+}
+
 template <typename Real, int R, typename TIN, typename TOUT>
 static cudaError_t launch_rt(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     using G = StencilGeom<Real, R, 1, 8, TIN>;
@@ -409,6 +534,24 @@ static cudaError_t launch_types(const SmoothArgs& a, int num_sms, cudaStream_t s
         case 6: return launch_rt<Real, 6, TIN, TOUT>(a, num_sms, s);
         case 7: return launch_rt<Real, 7, TIN, TOUT>(a, num_sms, s);
         case 8: return launch_rt<Real, 8, TIN, TOUT>(a, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool smooth_xy_supported(const SmoothArgs& a) {
+    return a.ncomp == 3 && a.in_type == kStoreF32 && a.out_type == kStoreF32 && a.taps.R >= 1 &&
+           a.taps.R <= 4;
+}
+
+cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s) {
+    if (!smooth_xy_supported(a)) return cudaErrorInvalidValue;
+    const long long tiles32 = (long long)((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + 31) / 32) * a.ncomp;
+    const bool tall = tiles32 * a.g.nz >= 8LL * num_sms;
+    switch (a.taps.R) {
+        case 1: return tall ? launch_sxy<1, 32>(a, num_sms, s) : launch_sxy<1, S2Y>(a, num_sms, s);
+        case 2: return tall ? launch_sxy<2, 32>(a, num_sms, s) : launch_sxy<2, S2Y>(a, num_sms, s);
+        case 3: return tall ? launch_sxy<3, 32>(a, num_sms, s) : launch_sxy<3, S2Y>(a, num_sms, s);
+        case 4: return tall ? launch_sxy<4, 32>(a, num_sms, s) : launch_sxy<4, S2Y>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -127,24 +127,31 @@ __device__ __forceinline__ void s2_edge_fix(float* slots, int slot_stride_floats
     __syncthreads();
 }
 
-// y pass of one plane into ring slot J (pair rows 2q + t and 2q + 1 + t, i.e.
-// rows (2q + t, 2q + TY/2 + t) and (2q + 1 + t, 2q + TY/2 + 1 + t))
-template <int R, int J>
-__device__ __forceinline__ void s2_y(const f32x2* __restrict__ txp, int q, int lx,
-                                     const f32x2 (&wp)[R + 1], f32x2 (&ring)[2 * R + 1][2]) {
+// y pass of one plane for thread (q, lx): p0 = rows (2q, 2q + TY/2) and
+// p1 = rows (2q + 1, 2q + TY/2 + 1) of column lx, from pair rows 2q + t and
+// 2q + 1 + t
+template <int R>
+__device__ __forceinline__ void s2_y_pair(const f32x2* __restrict__ txp, int q, int lx,
+                                          const f32x2 (&wp)[R + 1], f32x2& p0, f32x2& p1) {
     constexpr int K = 2 * R + 1;
     f32x2 in2[K + 1];
 #pragma unroll
     for (int m = 0; m < K + 1; ++m) in2[m] = txp[(2 * q + m) * S2TP + lx];
-    f32x2 p0 = 0ull, p1 = 0ull;
+    p0 = 0ull;
+    p1 = 0ull;
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         const f32x2 wt = wp[t <= R ? t : 2 * R - t];
         p0 = f2_fma(wt, in2[t], p0);
         p1 = f2_fma(wt, in2[t + 1], p1);
     }
-    ring[J][0] = p0;
-    ring[J][1] = p1;
+}
+
+// the same into ring slot J
+template <int R, int J>
+__device__ __forceinline__ void s2_y(const f32x2* __restrict__ txp, int q, int lx,
+                                     const f32x2 (&wp)[R + 1], f32x2 (&ring)[2 * R + 1][2]) {
+    s2_y_pair<R>(txp, q, lx, wp, ring[J][0], ring[J][1]);
 }
 
 // z pass over the ring whose newest plane is in slot J, oldest plane first:

@@ -57,7 +57,7 @@ def dl():
 
 def gpu_register(dl, S, M, variant, levels, iters, alpha=0.4, sigma=1.0, spacing=(1, 1, 2.5),
                  stop_mode=0, eps=1e-4, window=10, use_graph=1, on_device=True, init=None,
-                 timing=0, repeat=1, fp64=False, fuse=0, plain=0):
+                 timing=0, repeat=1, fp64=False, fuse=2, plain=0):
     params = dl.dir_params_default(levels=levels, iters=iters, alpha=alpha, sigma=sigma,
                                    stop_mode=stop_mode, eps=eps, stop_window=window,
                                    use_graph=use_graph, timing=timing, fuse=fuse,
@@ -341,13 +341,20 @@ def test_state_errors(dl, small_phantom):
     assert e.value.code == dlm.DIR_EINVAL
 
 
-@pytest.mark.parametrize("fuse", [1, 0])
+@pytest.mark.parametrize("fuse", [1, 0, 3])
 def test_timing_stats(dl, small_phantom, fuse):
     S, M = small_phantom["S"], small_phantom["M"]
     for graph in (1, 0):
         g = gpu_register(dl, S, M, 0, 2, [4, 7], timing=1, use_graph=graph, fuse=fuse)
         st = g["stats"]
-        if fuse:
+        assert st["schedule_finest"] == {0: 0, 1: 1, 3: 2}[fuse]
+        if fuse == 3:
+            # per level: plain force, then x/y + z/force kernels, one smoothing;
+            # the x/y and z/force launches of iterations > 0 are timed
+            assert st["n_force_finest"] == 6 and st["n_smooth_finest"] == 6
+            assert st["n_fused_finest"] == 0
+            assert st["kernel_launches"] == 2 * 2 + 1 + 2 * 4 + 2 * 7
+        elif fuse:
             # per level: plain force, fused iterations, one smoothing
             assert st["n_force_finest"] == 1 and st["n_fused_finest"] == 6
             assert st["n_smooth_finest"] == 1
@@ -529,11 +536,11 @@ def test_production_kernels_match_plain_kernels_full_size(dl, full_phantom, vari
 
 @pytest.mark.parametrize("variant", [0, 1])
 def test_fused_small_levels_match_plain_kernels(dl, full_phantom, variant):
-    # the default schedule's fused small-level iteration (the 64 x 64 x 25
-    # level of the full phantom; the 128 x 128 x 50 level runs the two-kernel
-    # production schedule) against the plain kernels
+    # the fused iteration: the small-level kernel on the 64 x 64 x 25 level of
+    # the full phantom and the marching one on the 128 x 128 x 50 level,
+    # against the plain kernels
     S, M = full_phantom["S"], full_phantom["M"]
-    _tight(dl, S, M, variant, 0.4, 3, [20, 10, 0], 2, f"3x20/10/0 fused v{variant}")
+    _tight(dl, S, M, variant, 0.4, 3, [20, 10, 0], 1, f"3x20/10/0 fused v{variant}")
 
 
 @pytest.mark.parametrize("variant,alpha", FULL_VARIANTS)
@@ -542,6 +549,75 @@ def test_production_kernels_match_plain_kernels_max_size(dl, wave_max, variant, 
     # field components, the largest grids)
     S, M = wave_max
     _tight(dl, S, M, variant, alpha, 1, [5], 0, f"512x512x160 v{variant} a{alpha}")
+
+
+# The split schedule (fuse = 3): the Gaussian's x and y passes as their own
+# kernel and its z pass inside the force kernel, for Eqs. 1-2.  Same
+# arithmetic per voxel as the two-kernel schedule, so bit for bit the plain
+# kernels' field.
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_split_schedule_matches_plain_kernels_full_size(dl, full_phantom, variant):
+    S, M = full_phantom["S"], full_phantom["M"]
+    _tight(dl, S, M, variant, 0.4, 3, [20, 10, 5], 3, f"3x20/10/5 split v{variant}")
+
+
+@pytest.mark.parametrize("dims", [(45, 37, 19), (70, 9, 33), (100, 60, 41), (160, 150, 48),
+                                  (33, 17, 65), (5, 7, 3), (1, 9, 8), (40, 1, 12), (24, 20, 1)])
+def test_split_schedule_ragged(dl, dims):
+    # partial tiles in x and y, bricks shallower than the z halo, volumes
+    # thinner than the Gaussian, one-voxel axes, three levels
+    from phantom import PhantomSpec, make_blob_pair, make_lung_phantom
+    if min(dims[:2]) > 1:
+        spec = PhantomSpec(dims=dims, spacing=(1.2, 1.2, 2.5), seed=31, a_max_mm=5.0,
+                           compression=0.1, n_vessels=12, n_landmarks=50)
+        p = make_lung_phantom(spec)
+        S, M = p["S"], p["M"]
+    else:
+        S, M = make_blob_pair(dims, (0.6, -0.4, 0.3), seed=5, n_blobs=8, sigma_vox=2.0, noise=0.3)
+    for variant in (0, 1):
+        _tight(dl, S, M, variant, 0.4, 3, [12, 8, 6], 3, f"{dims} split v{variant}")
+
+
+def test_split_schedule_with_stop_test(dl, small_phantom):
+    # the stop test ends a level early: the split kernels skip the rest and
+    # the last smoothing still runs on the last v
+    S, M = small_phantom["S"], small_phantom["M"]
+    kw = dict(stop_mode=1, eps=2e-3, window=10)
+    a = gpu_register(dl, S, M, 0, 2, [300, 300], fuse=3, **kw)
+    b = gpu_register(dl, S, M, 0, 2, [300, 300], plain=1, **kw)
+    runs = a["stats"]["iters_run"][:2]
+    assert runs == b["stats"]["iters_run"][:2] and min(runs) < 300, runs
+    assert np.array_equal(a["u"], b["u"])
+
+
+def test_split_schedule_int16_images(dl, full_phantom):
+    # int16 HU images through the split kernels: the field of float images
+    S = np.round(full_phantom["S"]).astype(np.int16)
+    M = np.round(full_phantom["M"]).astype(np.int16)
+    nz, ny, nx = S.shape
+    out = {}
+    for fuse, dt, (Si, Mi) in ((3, dl.DIR_I16, (S, M)),
+                               (0, dl.DIR_F32, (S.astype(np.float32), M.astype(np.float32)))):
+        params = dl.dir_params_default(levels=3, iters=[20, 10, 5], fuse=fuse)
+        ctx = dl.dir_create(torch.from_numpy(Si).cuda(), torch.from_numpy(Mi).cuda(),
+                            (nx, ny, nz), FULL_SPACING, dt, True, 0, params,
+                            torch.cuda.current_stream())
+        try:
+            st = dl.dir_register(ctx)
+            u = np.empty((3, nz, ny, nx), np.float32)
+            dl.dir_get_field(ctx, u)
+        finally:
+            dl.dir_destroy(ctx)
+        out[fuse] = (u, st.schedule_finest)
+    assert out[3][1] == 2 and out[0][1] == 0
+    assert np.array_equal(out[3][0], out[0][0])
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_split_schedule_matches_plain_kernels_max_size(dl, wave_max, variant):
+    S, M = wave_max
+    _tight(dl, S, M, variant, 0.4, 1, [5], 3, f"512x512x160 split v{variant}")
 
 
 # ------------------------------------------------------------ maximum size
@@ -625,8 +701,9 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable(dl, small_phantom):
 
 # ------------------------------------------------------- correlation coefficient
 
-@pytest.mark.parametrize("variant,fuse,plain", [(0, 0, 0), (0, 1, 0), (1, 1, 0), (2, 0, 0),
-                                                (5, 0, 0), (5, 0, 1), (3, 0, 1)])
+@pytest.mark.parametrize("variant,fuse,plain", [(0, 0, 0), (0, 1, 0), (1, 1, 0), (0, 3, 0),
+                                                (1, 3, 0), (2, 0, 0), (5, 0, 0), (5, 0, 1),
+                                                (3, 0, 1)])
 def test_correlation_matches_the_oracle(dl, small_phantom, variant, fuse, plain):
     # Secs. 2.4, 3.3: the correlation coefficient of the warped image with S
     # (Eq. 6: of the two warped images) every iteration, reduced on the device
