@@ -414,6 +414,11 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             xa.in = vbuf;
             xa.out = tbuf;
             xa.zchunk = c->tune_zchunk[l];  // 0: the launcher's own chunking
+            // brick depths: of the z + force kernel (tuned or its own rule), and
+            // of the plain force pass of iteration 0
+            const int zs_depth =
+                c->tune_depth[l] ? c->tune_depth[l] : dirk::force_zs_depth(c->variant, g, c->num_sms);
+            const int first_depth = dirk::force_brick_depth(g, c->num_sms);
             for (int it = 0; it < n; ++it, ++row) {
                 cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
                 if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -423,6 +428,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                 fa.v = vbuf;
                 if (it == 0) {
                     fa.u = cur;
+                    fa.depth = first_depth;
                     CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
                     c->launches += 1;
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -431,6 +437,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s));
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
                     fa.u = tbuf;
+                    fa.depth = zs_depth;
                     CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
                     c->launches += 2;
                 }
@@ -1211,7 +1218,9 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         const bool split = level_schedule(c, l) == 2;  // time the kernels the level runs
         float best = 1e30f;
         int best_d = 0;
-        for (int d = 1; d <= 8 && rc == DIR_OK; d *= 2) {
+        const int depths[5] = {1, 2, 4, 8, 6};  // 6: the split force kernel only
+        for (int di = 0; di < (split ? 5 : 4) && rc == DIR_OK; ++di) {
+            const int d = depths[di];
             fa.depth = d;
             float ms = 0.0f;
             rc = timed([&]() {

@@ -225,11 +225,23 @@ static cudaError_t launch_zs_types(int variant, const ForceArgs& a, const Taps& 
                                    cudaStream_t s) {
     switch (a.depth) {
         case 8: return variant ? launch_zs<1, 8, TI>(a, taps, s) : launch_zs<0, 8, TI>(a, taps, s);
+        case 6: return variant ? launch_zs<1, 6, TI>(a, taps, s) : launch_zs<0, 6, TI>(a, taps, s);
         case 4: return variant ? launch_zs<1, 4, TI>(a, taps, s) : launch_zs<0, 4, TI>(a, taps, s);
         case 2: return variant ? launch_zs<1, 2, TI>(a, taps, s) : launch_zs<0, 2, TI>(a, taps, s);
         case 1: return variant ? launch_zs<1, 1, TI>(a, taps, s) : launch_zs<0, 1, TI>(a, taps, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Brick depth: Eq. 1 takes 6 planes where that still gives four waves of
+// blocks -- the brick of t with its 2R halo planes and the S box then fit four
+// blocks per SM in shared memory instead of three (measured on 256x256x100:
+// 65.4 us against 70.3 us at depth 8); otherwise, and for Eq. 2 with its M box,
+// the force pass's usual depth.
+int force_zs_depth(int variant, const Grid3& g, int num_sms) {
+    const long long bxy = (long long)((g.nx + FTX - 1) / FTX) * ((g.ny + FTY - 1) / FTY);
+    if (variant == 0 && bxy * ((g.nz + 5) / 6) >= 4LL * 4 * num_sms) return 6;
+    return force_brick_depth(g, num_sms);
 }
 
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps) {

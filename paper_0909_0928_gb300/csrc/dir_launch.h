@@ -71,8 +71,9 @@ cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
 // Force pass of Eqs. 1-2 whose u is G_z * t, t = a.u the output of
 // launch_smooth_xy (single-precision field, float or int16 images, radius 3):
 // v = u - dr(u) and the reductions of ForceArgs, the same field bit for bit as
-// launch_smooth + launch_force.  Brick depth a.depth (8, 4, 2 or 1).
+// launch_smooth + launch_force.  Brick depth a.depth (8, 6, 4, 2 or 1).
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
+int force_zs_depth(int variant, const Grid3& g, int num_sms);
 cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
 
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
