@@ -104,18 +104,19 @@ typedef struct {
                                     precision for verification against an FP64 reference; it
                                     runs the plain-load kernels of plain_kernels = 1 in double,
                                     not the TMA-tiled single-precision kernels) */
-    int fuse;                    /* iteration schedule for Eqs. (1)-(2) (the same field bit for bit
-                                    in every schedule; Eqs. (3)-(6) always run force + smoothing).
+    int fuse;                    /* iteration schedule (the same field bit for bit in every one).
                                     0: a force kernel, then a smoothing kernel.  1: fused -- the
                                     Gaussian of iteration k folded into the force pass of
-                                    iteration k+1 (FP32 images and field, no stop test), every
-                                    level.  3: split -- the Gaussian's x and y passes as their own
-                                    kernel plane by plane, its z pass inside the force kernel down
-                                    each thread's z column (FP32 field, float or int16 images,
-                                    sigma with radius 3, any stop_mode), every level.  2
-                                    (default): split where it applies, else fused on the small
-                                    levels that one block per SM covers in two-plane chunks (e.g.
-                                    64 x 64 x 25), else 0 */
+                                    iteration k+1 (Eqs. (1)-(2), FP32 images and field, no stop
+                                    test), every level.  3: split -- the Gaussian's x and y passes
+                                    as their own kernel plane by plane, its z pass inside the
+                                    force kernel down each thread's z column (all six laws, FP32
+                                    field, float or int16 images, sigma with radius 3, any
+                                    stop_mode), every level.  2 (default): split for Eqs.
+                                    (1)-(2) on every level and for Eqs. (3)-(6) on levels of at
+                                    most 2^21 voxels, else fused on the small levels that one
+                                    block per SM covers in two-plane chunks (e.g. 64 x 64 x 25),
+                                    else 0 */
     int plain_kernels;           /* 0 (default): the production kernels (TMA-fed bricks and
                                     plane rings, packed smoothing, fused small levels).  1: the
                                     plain-load kernels with the same per-voxel arithmetic and

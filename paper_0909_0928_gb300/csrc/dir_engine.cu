@@ -245,22 +245,30 @@ static int record(dir_ctx* c, cudaEvent_t e, cudaStream_t s, bool capturing) {
 // iteration (the Gaussian of v_{k-1} folded into the force pass), 2 split
 // Gaussian (its x and y passes as their own kernel, its z pass inside the
 // force kernel).  All three give the same field bit for bit.  fuse = 2 (the
-// default) takes the split schedule where it applies (Eqs. 1-2, FP32 field,
-// radius 3) and otherwise the fused one on the small levels: measured on the
-// 256x256x100 pyramid, the split schedule is fastest on every level.
+// default) takes the split schedule where it applies (FP32 field, radius 3) for
+// Eqs. 1-2 on every level and for Eqs. 3-6 on the small levels, otherwise the
+// fused one on the small levels: measured per level on the 256x256x100 pyramid.
 static int level_schedule(const dir_ctx* c, int l) {
     if (c->fp64 || c->p.plain_kernels) return 0;
     const Grid3& g = c->lv[l].g;
-    const bool split_ok = c->field_type == dirk::kStoreF32 && (c->variant == 0 || c->variant == 1) &&
+    const bool split_ok = c->field_type == dirk::kStoreF32 &&
                           (c->img_type(l) == dirk::kStoreF32 || c->img_type(l) == dirk::kStoreI16) &&
                           c->taps.R == 3;
+    const bool eqs12 = c->variant == 0 || c->variant == 1;
     const bool fused_ok = c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
                           c->field_type == c->real_type && c->img_type(l) == c->real_type;
     switch (c->p.fuse) {
         case 1: return fused_ok ? 1 : 0;
-        case 2:
-            if (split_ok) return 2;
+        case 2: {
+            // Eqs. 3-6 need u on the brick's one-voxel halo too, so their split
+            // kernel runs the z pass on 34 x 10 columns of a deeper box: it pays
+            // on levels of at most 2^21 voxels (the marching smoothing's z halo
+            // costs more there) and not above (256x256x100, active: 137 us
+            // against 98 + 54 - 37 us per finest iteration)
+            const bool small = (long long)g.nx * g.ny * g.nz <= (1LL << 21);
+            if (split_ok && (eqs12 || small)) return 2;
             return fused_ok && dirk::fused_small_level(g, c->num_sms) ? 1 : 0;
+        }
         case 3: return split_ok ? 2 : 0;
         default: return 0;
     }

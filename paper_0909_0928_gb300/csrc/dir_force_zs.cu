@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "dir_force_gm.cuh"
 #include "dir_force_kernel.cuh"
 #include "dir_stencil.cuh"
 
@@ -180,6 +181,110 @@ __global__ void __launch_bounds__(FNT, 4)
     if (a.corr) block_reduce4_atomic<FNT, float>(corr_s, a.corr);
 }
 
+// ---------------------------------------------------------------------------
+// Eqs. (3)-(6) split the same way.  Their force needs the gradient of the
+// warped image, so u is needed on the brick plus a one-voxel halo: the block
+// copies t over the u box of force_tma_gm_kernel (x0 - 4 .. x0 + 35,
+// y0 - 1 .. y0 + 8) with R + 1 extra planes below and above, forms
+// u = G_z * t in place on the 34 x 10 columns the force reads (one thread per
+// column, a column read and written only by its thread), and then runs the
+// Eqs. 3-6 force work of dir_force_gm.cuh on that u.
+// ---------------------------------------------------------------------------
+template <int FTZ, int V, typename TI>
+struct GZGeom {
+    using G = FGGeom<FTZ, V, TI>;
+    static constexpr int NPZ = G::UD + 2 * FZR;   // t planes z0 - 1 - R .. z0 + FTZ + R
+    static constexpr int PL = G::UH * G::UW;      // floats per plane of the box
+    static constexpr int TBOX = 3 * NPZ * PL * 4;
+    static constexpr int OFF_S = (TBOX + 127) / 128 * 128;
+    static constexpr int OFF_W = OFF_S + (G::SBOX + 127) / 128 * 128;
+    static constexpr int OFF_BAR = OFF_W + (G::WT + 127) / 128 * 128;
+    static constexpr int SMEM = 128 + OFF_BAR + 64;
+};
+
+template <int V, int FTZ, typename TI>
+__global__ void __launch_bounds__(FNT, FTZ >= 2 ? 3 : 4)
+    force_gzs_kernel(const __grid_constant__ CUtensorMap tmap,
+                     const __grid_constant__ CUtensorMap smap,
+                     const __grid_constant__ CUtensorMap mmap, const ForceArgs a, const Taps taps) {
+    static_assert(V >= 2 && V <= 5, "Eqs. 3-6");
+    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;  // uniform across the grid
+    using F = FGGeom<FTZ, V, TI>;
+    using Z = GZGeom<FTZ, V, TI>;
+    constexpr int R = FZR, NPZ = Z::NPZ, PL = Z::PL, UD = F::UD, FBX = F::FBX;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float* tb = reinterpret_cast<float*>(base);                   // [3][NPZ][UH][UW]
+    const TI* sb = reinterpret_cast<const TI*>(base + Z::OFF_S);  // [UD][FSH][FSW]
+    float* wt = reinterpret_cast<float*>(base + Z::OFF_W);        // [HZ][HY][HX]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + Z::OFF_BAR);
+    const Grid3 g = a.g;
+    const int tid = threadIdx.x + FTX * threadIdx.y;
+    const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
+    const int zlo = bz0 - 1 - R;  // global plane of box plane 0
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, (uint32_t)(Z::TBOX + F::SBOX));
+        tma_load_4d(base, &tmap, bx0 - 4, by0 - 1, zlo, 0, bar);
+        tma_load_4d(base + Z::OFF_S, &smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
+        if (a.pf_stride > 0) {  // the block pf_stride positions ahead: its boxes into L2
+            const long long gx = gridDim.x, gy = gridDim.y;
+            const long long b = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) +
+                                a.pf_stride;
+            if (b < gx * gy * gridDim.z) {
+                const int px = (int)(b % gx) * FTX, py = (int)((b / gx) % gy) * FTY;
+                const int pz = (int)(b / (gx * gy)) * FTZ;
+                tma_prefetch_4d(&tmap, px - 4, py - 1, pz - 1 - R, 0);
+                tma_prefetch_4d(&smap, px - FBX, py - 1, pz - 1, 0);
+                tma_prefetch_4d(&mmap, px - FBX, py - 1, pz - 1, 0);
+            }
+        }
+    }
+    __syncthreads();
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
+        return;
+    }
+    (void)mbar_try_wait(bar, 0);
+
+    // z pass on the columns x0 - 1 .. x0 + 32 (box columns 3 .. 36), all rows;
+    // planes outside the volume arrive zero-filled and are replicated first
+    float w[R + 1];
+#pragma unroll
+    for (int t = 0; t <= R; ++t) w[t] = taps.wf[t];
+    constexpr int NCX = FTX + 2, NCOL = NCX * F::UH;
+    const bool zedge = zlo < 0 || zlo + NPZ > g.nz;
+    const int jlo = max(0, -zlo), jhi = min(NPZ - 1, g.nz - 1 - zlo);
+    for (int col = tid; col < NCOL; col += FNT) {
+        float* tcol = tb + (col / NCX) * F::UW + 3 + (col % NCX);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float* tc = tcol + c * NPZ * PL;
+            if (zedge) {
+                const float lo = tc[jlo * PL], hi = tc[jhi * PL];
+                for (int j = 0; j < jlo; ++j) tc[j * PL] = lo;
+                for (int j = jhi + 1; j < NPZ; ++j) tc[j * PL] = hi;
+            }
+            float cv[NPZ];
+#pragma unroll
+            for (int j = 0; j < NPZ; ++j) cv[j] = tc[j * PL];
+#pragma unroll
+            for (int k = 0; k < UD; ++k) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int t = 0; t < 2 * R + 1; ++t) acc = fmaf(w[t <= R ? t : 2 * R - t], cv[k + t], acc);
+                tc[(R + k) * PL] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    gm_force_body<V, FTZ, TI, NPZ * PL>(a, tb + R * PL, sb, wt);
+}
+
 template <typename TI>
 static bool make_zs_maps(CUtensorMap* tmap, CUtensorMap* smap, CUtensorMap* mmap,
                          const ForceArgs& a, int ftz) {
@@ -233,6 +338,65 @@ static cudaError_t launch_zs_types(int variant, const ForceArgs& a, const Taps& 
     }
 }
 
+template <int V, int FTZ, typename TI>
+static cudaError_t launch_gzs(const ForceArgs& a, const Taps& taps, cudaStream_t s) {
+    using F = FGGeom<FTZ, V, TI>;
+    using Z = GZGeom<FTZ, V, TI>;
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorInvalidValue;
+    const Grid3& g = a.g;
+    const cuuint64_t tdims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 3};
+    const cuuint64_t idims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 1};
+    const cuuint64_t tstr[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                (cuuint64_t)g.cs * 4};
+    const cuuint64_t istr[3] = {(cuuint64_t)g.px * sizeof(TI), (cuuint64_t)g.plane * sizeof(TI),
+                                (cuuint64_t)g.cs * sizeof(TI)};
+    const cuuint32_t tbox[4] = {(cuuint32_t)F::UW, (cuuint32_t)F::UH, (cuuint32_t)Z::NPZ, 3u};
+    const cuuint32_t ibox[4] = {(cuuint32_t)F::FSW, (cuuint32_t)FSH, (cuuint32_t)F::UD, 1u};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    auto enc4 = [&](CUtensorMap* m, CUtensorMapDataType t, const void* p, const cuuint64_t* d,
+                    const cuuint64_t* st, const cuuint32_t* b) {
+        return enc(m, t, 4, const_cast<void*>(p), d, st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap tmap, smap, mmap;
+    if (!enc4(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a.u, tdims, tstr, tbox) ||
+        !enc4(&smap, tma_type<TI>(), a.S, idims, istr, ibox) ||
+        !enc4(&mmap, tma_type<TI>(), a.M, idims, istr, ibox))
+        return cudaErrorInvalidValue;
+    static KernelSetup setup;  // per instantiation
+    const cudaError_t e = setup_kernel(setup, force_gzs_kernel<V, FTZ, TI>, Z::SMEM);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((g.nx + FTX - 1) / FTX, (g.ny + FTY - 1) / FTY, (g.nz + FTZ - 1) / FTZ);
+    force_gzs_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), Z::SMEM, s>>>(tmap, smap, mmap, a, taps);
+    return cudaGetLastError();
+}
+
+template <int V, typename TI>
+static cudaError_t launch_gzs_depth(const ForceArgs& a, const Taps& taps, cudaStream_t s) {
+    switch (a.depth) {
+        case 8:
+        case 6:
+        case 4: return launch_gzs<V, 4, TI>(a, taps, s);  // at most 4 deep, as force_tma_gm_kernel
+        case 2: return launch_gzs<V, 2, TI>(a, taps, s);
+        case 1: return launch_gzs<V, 1, TI>(a, taps, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TI>
+static cudaError_t launch_gzs_types(int variant, const ForceArgs& a, const Taps& taps,
+                                    cudaStream_t s) {
+    switch (variant) {
+        case 2: return launch_gzs_depth<2, TI>(a, taps, s);
+        case 3: return launch_gzs_depth<3, TI>(a, taps, s);
+        case 4: return launch_gzs_depth<4, TI>(a, taps, s);
+        case 5: return launch_gzs_depth<5, TI>(a, taps, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // Brick depth: Eq. 1 takes 6 planes where that still gives four waves of
 // blocks -- the brick of t with its 2R halo planes and the S box then fit four
 // blocks per SM in shared memory instead of three (measured on 256x256x100:
@@ -245,12 +409,16 @@ int force_zs_depth(int variant, const Grid3& g, int num_sms) {
 }
 
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps) {
-    return (variant == 0 || variant == 1) && a.field_type == kStoreF32 &&
+    return variant >= 0 && variant <= 5 && a.field_type == kStoreF32 &&
            (a.img_type == kStoreF32 || a.img_type == kStoreI16) && taps.R == FZR;
 }
 
 cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s) {
     if (!force_zs_supported(variant, a, taps)) return cudaErrorInvalidValue;
+    if (variant >= 2) {
+        if (a.img_type == kStoreF32) return launch_gzs_types<float>(variant, a, taps, s);
+        return launch_gzs_types<int16_t>(variant, a, taps, s);
+    }
     if (a.img_type == kStoreF32) return launch_zs_types<float>(variant, a, taps, s);
     return launch_zs_types<int16_t>(variant, a, taps, s);
 }

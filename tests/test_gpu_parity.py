@@ -556,10 +556,19 @@ def test_production_kernels_match_plain_kernels_max_size(dl, wave_max, variant, 
 # arithmetic per voxel as the two-kernel schedule, so bit for bit the plain
 # kernels' field.
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_split_schedule_matches_plain_kernels_full_size(dl, full_phantom, variant):
     S, M = full_phantom["S"], full_phantom["M"]
     _tight(dl, S, M, variant, 0.4, 3, [20, 10, 5], 3, f"3x20/10/5 split v{variant}")
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
+def test_default_schedule_matches_plain_kernels_full_size(dl, full_phantom, variant):
+    # the default for Eqs. 3-6: split on the two coarse levels, force +
+    # smoothing kernels on the finest; the field crosses between schedules at
+    # each upsampling
+    S, M = full_phantom["S"], full_phantom["M"]
+    _tight(dl, S, M, variant, 0.4, 3, [20, 10, 5], 2, f"3x20/10/5 default v{variant}")
 
 
 @pytest.mark.parametrize("dims", [(45, 37, 19), (70, 9, 33), (100, 60, 41), (160, 150, 48),
@@ -575,7 +584,7 @@ def test_split_schedule_ragged(dl, dims):
         S, M = p["S"], p["M"]
     else:
         S, M = make_blob_pair(dims, (0.6, -0.4, 0.3), seed=5, n_blobs=8, sigma_vox=2.0, noise=0.3)
-    for variant in (0, 1):
+    for variant in (0, 1, 3, 5):
         _tight(dl, S, M, variant, 0.4, 3, [12, 8, 6], 3, f"{dims} split v{variant}")
 
 
@@ -614,7 +623,7 @@ def test_split_schedule_int16_images(dl, full_phantom):
     assert np.array_equal(out[3][0], out[0][0])
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3, 5])
 def test_split_schedule_matches_plain_kernels_max_size(dl, wave_max, variant):
     S, M = wave_max
     _tight(dl, S, M, variant, 0.4, 1, [5], 3, f"512x512x160 split v{variant}")
