@@ -61,7 +61,11 @@ __global__ void __launch_bounds__(FNT, 4)
     const TI* __restrict__ M = static_cast<const TI*>(a.M);
     float* __restrict__ v = static_cast<float*>(a.v);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + FTX * ty;
-    const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
+    // bricks from the top plane down: smooth_xy_kernel wrote t bottom up, so
+    // the first bricks find the planes it wrote last still in L2, and the next
+    // x/y pass (bottom up) finds the v this kernel wrote last
+    const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY;
+    const int bz0 = (gridDim.z - 1 - blockIdx.z) * FTZ;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(FNT, 4)
                                 a.pf_stride;
             if (b < gx * gy * gridDim.z) {
                 const int px = (int)(b % gx) * FTX, py = (int)((b / gx) % gy) * FTY;
-                const int pz = (int)(b / (gx * gy)) * FTZ;
+                const int pz = (int)(gridDim.z - 1 - b / (gx * gy)) * FTZ;
                 tma_prefetch_4d(&tmap, px, py, pz - R, 0);
                 tma_prefetch_4d(&smap, px - FBX, py - 1, pz - 1, 0);
                 tma_prefetch_4d(&mmap, px - FBX, py - 1, pz - 1, 0);
