@@ -98,10 +98,10 @@ def measured_peak_gbs():
 # is valid only while their combined sha256 is unchanged)
 KERNEL_SOURCES = {
     "force_kernel": ["dir_force_kernel.cuh", "dir_force_law.cuh", "dir_common.cuh"],
-    "force_tma_kernel": ["dir_force_tma.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
-                         "dir_stencil.cuh", "dir_common.cuh"],
-    "force_tma_gm_kernel": ["dir_force_tma.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
-                            "dir_stencil.cuh", "dir_common.cuh"],
+    "force_tma_kernel": ["dir_force_tma.cu", "dir_force_gm.cuh", "dir_force_kernel.cuh",
+                         "dir_force_law.cuh", "dir_stencil.cuh", "dir_common.cuh"],
+    "force_tma_gm_kernel": ["dir_force_tma.cu", "dir_force_gm.cuh", "dir_force_kernel.cuh",
+                            "dir_force_law.cuh", "dir_stencil.cuh", "dir_common.cuh"],
     "smooth2_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
     "fused_kernel": ["dir_fused.cu", "dir_stencil.cuh", "dir_force_law.cuh", "dir_common.cuh"],
     "fused2_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
@@ -109,8 +109,8 @@ KERNEL_SOURCES = {
     "fused_small_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
                            "dir_force_law.cuh", "dir_common.cuh"],
     "smooth_xy_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
-    "force_zs_kernel": ["dir_force_zs.cu", "dir_force_kernel.cuh", "dir_force_law.cuh",
-                        "dir_stencil.cuh", "dir_common.cuh"],
+    "force_zs_kernel": ["dir_force_zs.cu", "dir_force_gm.cuh", "dir_force_kernel.cuh",
+                        "dir_force_law.cuh", "dir_stencil.cuh", "dir_common.cuh"],
 }
 
 
