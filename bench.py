@@ -271,12 +271,28 @@ def _batch_pair(k):
             0 if k % 2 == 0 else 5)
 
 
-def batch_pairs(n=BATCH_PAIRS):
+SMALL_PAIRS = 64
+SMALL_DIMS = (64, 64, 32)
+
+
+def _small_pair(k):
+    """Pair k of the small-volume batch: the 64x64x32 phantom shape (1 x 1 x 2.5
+    mm, RBF motion up to 4 mm) with seed 300 + k, int16 HU; passive for even k,
+    inverse consistent for odd k."""
+    import numpy as np
+    from phantom import PhantomSpec, make_lung_phantom
+    ph = make_lung_phantom(PhantomSpec(dims=SMALL_DIMS, spacing=(1.0, 1.0, 2.5), seed=300 + k,
+                                       a_max_mm=4.0, compression=0.05, n_landmarks=10))
+    return (np.round(ph["S"]).astype(np.int16), np.round(ph["M"]).astype(np.int16),
+            0 if k % 2 == 0 else 5)
+
+
+def batch_pairs(n=BATCH_PAIRS, small=False):
     """The 32 seeded pairs of uneven sizes, generated on the host cores by a
     pool started with spawn before any GPU work."""
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(min(n, os.cpu_count() or 1)) as pool:
-        return pool.map(_batch_pair, range(n))
+        return pool.map(_small_pair if small else _batch_pair, range(n))
 
 
 def run_batch(args):
@@ -287,6 +303,7 @@ def run_batch(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.current_stream()
     pairs = batch_pairs()
+    small = batch_pairs(SMALL_PAIRS, small=True)
     ctxs, dev, vu = [], [], 0
     for S, M, v in pairs:
         nz, ny, nx = S.shape
@@ -322,10 +339,19 @@ def run_batch(args):
     tune_s = time.perf_counter() - t0
     sequential(1)
     tuned_ms, _ = sequential(args.steps)
+    def fields_same():
+        ok = True
+        for (S, _, _), c, f0 in zip(pairs, ctxs, ref):
+            f = np.empty((3,) + S.shape, np.float32)
+            dl.dir_get_field(c, f)
+            ok = ok and bool(np.array_equal(f, f0))
+        return ok
+
+    # branch form: each registration on one of `br` concurrent graph branches
     best = None
     per_branches = {}
     for br in (4, 8, 16, 32):
-        b = dl.dir_batch_create(ctxs, branches=br, stream=stream)
+        b = dl.dir_batch_create(ctxs, branches=br, stream=stream, grouped=False)
         for _ in range(args.warmup):
             dl.dir_batch_run(b)
         ms = statistics.median([dl.dir_batch_run(b) for _ in range(args.steps)])
@@ -333,14 +359,65 @@ def run_batch(args):
         if best is None or ms < per_branches[best]:
             best = br
         dl.dir_batch_destroy(b)
-    clk = clocks.stop()
-    same = True
-    for (S, _, _), c, f0 in zip(pairs, ctxs, ref):
-        f = np.empty((3,) + S.shape, np.float32)
-        dl.dir_get_field(c, f)
-        same = same and bool(np.array_equal(f, f0))
+    same = fields_same()
+    # grouped form (the default): one x/y and one z + force launch per
+    # iteration over all the pairs of a pyramid level
+    b = dl.dir_batch_create(ctxs, stream=stream)
+    grouped = dl.dir_batch_grouped(b)
+    for _ in range(args.warmup):
+        dl.dir_batch_run(b)
+    gms = statistics.median([dl.dir_batch_run(b) for _ in range(args.steps)])
+    dl.dir_batch_destroy(b)
+    same = same and fields_same()
     for c in ctxs:
         dl.dir_destroy(c)
+
+    # many small volumes: one registration alone is bound by launch latencies
+    sctx, sdev, svu = [], [], 0
+    for S, M, v in small:
+        nz, ny, nx = S.shape
+        St, Mt = torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda()
+        sdev.append((St, Mt))
+        p = dl.dir_params_default(levels=LEVELS, iters=ITERS)
+        sctx.append(dl.dir_create(St, Mt, (nx, ny, nz), (1.0, 1.0, 2.5), dl.DIR_I16, True, v, p,
+                                  stream))
+        svu += voxel_updates((nx, ny, nz), LEVELS, ITERS)
+    for c in sctx:
+        dl.dir_register(c)
+    s_plain = statistics.median([sum(dl.dir_register(c).ms_total for c in sctx)
+                                 for _ in range(max(1, args.steps // 2))])
+    s_ref = []
+    for (S, _, _), c in zip(small, sctx):
+        f = np.empty((3,) + S.shape, np.float32)
+        dl.dir_get_field(c, f)
+        s_ref.append(f)
+    s_forms = {}
+    for name, kw in (("grouped", {}), ("branches_16", {"branches": 16, "grouped": False}),
+                     ("branches_32", {"branches": 32, "grouped": False})):
+        b = dl.dir_batch_create(sctx, stream=stream, **kw)
+        for _ in range(args.warmup):
+            dl.dir_batch_run(b)
+        s_forms[name] = statistics.median([dl.dir_batch_run(b) for _ in range(args.steps)])
+        dl.dir_batch_destroy(b)
+        for (S, _, _), c, f0 in zip(small, sctx, s_ref):
+            f = np.empty((3,) + S.shape, np.float32)
+            dl.dir_get_field(c, f)
+            same = same and bool(np.array_equal(f, f0))
+    for c in sctx:
+        dl.dir_destroy(c)
+    small_line = {"pairs": len(small), "dims": list(SMALL_DIMS),
+                  "sizes": "seeds 300-363, 64x64x32 int16 HU, passive / inverse consistent "
+                           "alternating, 3 levels 200/100/50",
+                  "voxel_updates": svu,
+                  "plain_sequential_ms": s_plain,
+                  "forms_ms": s_forms,
+                  "volumes_per_s": {k: len(small) / (v / 1e3) for k, v in
+                                    dict(s_forms, plain_sequential=s_plain).items()},
+                  "speedup_grouped_vs_plain": s_plain / s_forms["grouped"],
+                  "speedup_grouped_vs_best_branches": min(s_forms["branches_16"],
+                                                          s_forms["branches_32"]) /
+                                                      s_forms["grouped"]}
+    clk = clocks.stop()
     bms = per_branches[best]
     q = lambda xs, p: float(np.quantile(np.asarray(xs), p))
     line = {"mode": "batch", "pairs": n, "variants": {"passive": sum(v == 0 for *_, v in pairs),
@@ -354,12 +431,16 @@ def run_batch(args):
                                  "completion_p50_ms": q(plain_done, 0.5),
                                  "completion_p99_ms": q(plain_done, 0.99)},
             "tuned_sequential": {"ms": tuned_ms, "volumes_per_s": n / (tuned_ms / 1e3)},
-            "batched": {"ms": bms, "branches": best, "volumes_per_s": n / (bms / 1e3),
-                        "voxel_updates_per_s": vu / (bms / 1e3),
-                        "completion_p50_ms": bms, "completion_p99_ms": bms,
-                        "per_branch_count_ms": per_branches},
-            "speedup_vs_plain": plain_ms / bms, "fields_identical": same,
-            "autotune_s": tune_s, "tuned_shapes_first_pair": shapes[0], "clocks": clk}
+            "batched": {"ms": gms, "form": "grouped" if grouped else "branches (not groupable)",
+                        "volumes_per_s": n / (gms / 1e3), "voxel_updates_per_s": vu / (gms / 1e3),
+                        "completion_p50_ms": gms, "completion_p99_ms": gms},
+            "batched_branches": {"ms": bms, "branches": best, "volumes_per_s": n / (bms / 1e3),
+                                 "voxel_updates_per_s": vu / (bms / 1e3),
+                                 "per_branch_count_ms": per_branches},
+            "speedup_vs_plain": plain_ms / gms, "speedup_branches_vs_plain": plain_ms / bms,
+            "fields_identical": same,
+            "autotune_s": tune_s, "tuned_shapes_first_pair": shapes[0],
+            "small_volumes": small_line, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0 if same else 1
 

@@ -258,19 +258,34 @@ int dir_warp(dir_ctx* ctx, const void* img_in, void* img_out, dir_dtype dt, int 
 /*
  * Batched registration: one CUDA graph that runs the registrations of n
  * contexts (each created with dir_create, params.timing 0, none pending),
- * spread over `branches` concurrent branches (longest job first onto the least
- * loaded branch), replayed by one graph launch on cuda_stream.  Small volumes
- * and coarse pyramid levels, each too small to fill the GPU alone, run
- * together.  The contexts stay owned by the caller and must outlive the batch;
- * after dir_batch_run each context's field, history and warp are available as
- * after dir_register.  dir_batch_run waits for the batch and reports its
- * device time in *ms_out (may be NULL).  Multi-job batching of this kind is
- * beyond the paper, which registers one pair at a time.
+ * replayed by one graph launch on cuda_stream.  The contexts stay owned by the
+ * caller and must outlive the batch; after dir_batch_run each context's field,
+ * history and warp are available as after dir_register, bit for bit the same.
+ * dir_batch_run waits for the batch and reports its device time in *ms_out
+ * (may be NULL).  Multi-job batching of this kind is beyond the paper, which
+ * registers one pair at a time (each of its steps runs per pair here too).
+ *
+ * Two forms:
+ *  - grouped (the default where every context allows it: FP32 field, sigma
+ *    with radius 3, stop_mode 0, fuse 2 or 3, the same levels and iteration
+ *    counts): every iteration of a pyramid level is one x/y launch and one
+ *    z + force launch over the bricks of all the contexts at that level (up
+ *    to 16 per launch, grouped by force law and image storage) in the split
+ *    schedule of params.fuse, so the fixed latencies of a launch are paid
+ *    once per step for the whole chunk.  Each chunk runs on its own graph
+ *    branch (`branches` is then the number of chunks).  The pyramid, the
+ *    first force pass and the last smoothing of each level run per context;
+ *  - branches (flags & DIR_BATCH_BRANCHES, or when the contexts do not
+ *    qualify): each context's own registration on one of `branches`
+ *    concurrent graph branches (longest job first onto the least loaded).
  */
+#define DIR_BATCH_BRANCHES 1
 typedef struct dir_batch dir_batch;
-int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, int branches,
+int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, int branches, int flags,
                      void* cuda_stream);
 int dir_batch_run(dir_batch* batch, float* ms_out);
+/* 1 if the batch was captured in the grouped form, 0 for branches, -1 for NULL */
+int dir_batch_grouped(const dir_batch* batch);
 void dir_batch_destroy(dir_batch* batch);  /* NULL-safe */
 
 /*

@@ -9,7 +9,7 @@ importing this package raises.
 Functions carry the C names: dir_params_default, dir_create, dir_load,
 dir_register, dir_register_async, dir_sync, dir_get_field, dir_get_field_f64,
 dir_get_history, dir_get_correlation, dir_warp, dir_destroy, dir_status_string, dir_last_error, dir_version,
-dir_register_noalloc, dir_batch_create, dir_batch_run, dir_batch_destroy,
+dir_register_noalloc, dir_batch_create, dir_batch_run, dir_batch_grouped, dir_batch_destroy,
 dir_autotune, dir_check_wait_timeout.
 `Registration` wraps a context for convenience.
 """
@@ -37,7 +37,8 @@ EXPORTS = ["dir_params_default", "dir_create", "dir_load", "dir_register", "dir_
            "dir_sync", "dir_get_field", "dir_get_field_f64", "dir_get_history",
            "dir_get_correlation", "dir_warp", "dir_destroy",
            "dir_status_string", "dir_last_error", "dir_version", "dir_register_noalloc",
-           "dir_batch_create", "dir_batch_run", "dir_batch_destroy", "dir_autotune",
+           "dir_batch_create", "dir_batch_run", "dir_batch_grouped", "dir_batch_destroy",
+           "dir_autotune",
            "dir_check_wait_timeout"]
 
 
@@ -103,8 +104,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "dir_version": (C.c_char_p, []),
         "dir_register_noalloc": (ip, [vp, vp, C.POINTER(C.c_int * 3), ip, C.POINTER(DirParams),
                                       vp, vp, C.POINTER(DirStats)]),
-        "dir_batch_create": (ip, [C.POINTER(vp), C.POINTER(vp), ip, ip, vp]),
+        "dir_batch_create": (ip, [C.POINTER(vp), C.POINTER(vp), ip, ip, ip, vp]),
         "dir_batch_run": (ip, [vp, C.POINTER(C.c_float)]),
+        "dir_batch_grouped": (ip, [vp]),
         "dir_batch_destroy": (None, [vp]),
         "dir_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
         "dir_check_wait_timeout": (ip, [vp, C.c_double]),
@@ -316,14 +318,25 @@ def dir_check_wait_timeout(stream=None, limit_ms: float = 100.0) -> int:
     return int(_lib.dir_check_wait_timeout(_stream_handle(stream), float(limit_ms)))
 
 
-def dir_batch_create(ctxs, branches: int = 8, stream=None):
+DIR_BATCH_BRANCHES = 1
+
+
+def dir_batch_create(ctxs, branches: int = 8, stream=None, grouped: bool = True):
     """One captured CUDA graph that runs the registrations of `ctxs` (contexts
-    from dir_create) on `branches` concurrent branches."""
+    from dir_create): grouped launches per iteration where the contexts allow
+    it (and `grouped`), else each registration on one of `branches`
+    concurrent branches."""
     arr = (C.c_void_p * len(ctxs))(*ctxs)
     out = C.c_void_p()
-    _check(_lib.dir_batch_create(C.byref(out), arr, len(ctxs), int(branches),
+    flags = 0 if grouped else DIR_BATCH_BRANCHES
+    _check(_lib.dir_batch_create(C.byref(out), arr, len(ctxs), int(branches), flags,
                                  _stream_handle(stream)), "dir_batch_create")
     return out
+
+
+def dir_batch_grouped(batch) -> bool:
+    """True if the batch was captured in the grouped form."""
+    return int(_lib.dir_batch_grouped(batch)) == 1
 
 
 def dir_batch_run(batch) -> float:

@@ -347,6 +347,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Position of a block in its own launch grid: the whole launch, or one job's
+// share of a grouped launch over several volumes.
+struct BlockPos {
+    int x, y, z;     // block coordinates
+    int gx, gy, gz;  // grid extent
+    __device__ __forceinline__ static BlockPos of_grid() {
+        return {(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                (int)gridDim.x,  (int)gridDim.y,  (int)gridDim.z};
+    }
+};
+
 // 4-D tiled tensor load global -> shared, completing on `bar`.
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
                                             int c2, int c3, uint64_t* bar) {

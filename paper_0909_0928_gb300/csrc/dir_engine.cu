@@ -274,7 +274,10 @@ static int level_schedule(const dir_ctx* c, int l) {
     }
 }
 
-static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
+// The start of every registration: the reduction rows, stop flags and error
+// word cleared, and the pyramid (Sec. 2.3: level l+1 = unit-sigma Gaussian of
+// level l at even indices).
+static int enqueue_prologue(dir_ctx* c, cudaStream_t s) {
     c->launches = 0;
     const int L = c->levels;
     const bool f64 = c->fp64;
@@ -286,8 +289,6 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                               s));
     CK(c, cudaMemsetAsync(c->ctl, 0x7f, sizeof(int) * (size_t)L, s));
     CK(c, cudaMemsetAsync(c->derr, 0, sizeof(int), s));
-
-    // pyramid (Sec. 2.3): level l+1 = unit-sigma Gaussian of level l at even indices
     for (int l = 1; l < L; ++l) {
         const Grid3& gf = c->lv[l - 1].g;
         const Grid3& gc = c->lv[l].g;
@@ -309,7 +310,90 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             c->launches += 2;
         }
     }
+    return DIR_OK;
+}
 
+// The field at the start of level lc (coarsest first): the initial field or
+// zero on the coarsest level, else the upsampled field of the level before;
+// cur holds it afterwards, oth is free.
+static int enqueue_level_start(dir_ctx* c, int lc, char*& cur, char*& oth, cudaStream_t s) {
+    const int l = c->levels - 1 - lc;
+    const Grid3& g = c->lv[l].g;
+    if (lc == 0) {
+        if (c->p.init_field) {
+            const int rc = import_dense(c, c->p.init_field, 1, 4, cur, c->field_type, g, 3, s);
+            if (rc != DIR_OK) return rc;
+            if (c->field_type != dirk::kStoreF32) c->launches += 1;
+        } else {
+            CK(c, cudaMemsetAsync(cur, 0, c->fesz * 3 * (size_t)g.cs, s));
+        }
+    } else {
+        CK(c, dirk::launch_upsample(c->fp64, c->field_type, cur, c->lv[l + 1].g, oth, g, s));
+        c->launches += 1;
+        char* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    return DIR_OK;
+}
+
+// Force and smoothing arguments of level lc (buffers, rows and iteration set
+// by the caller)
+static dirk::ForceArgs level_force_args(const dir_ctx* c, int lc) {
+    const int l = c->levels - 1 - lc;
+    const Grid3& g = c->lv[l].g;
+    dirk::ForceArgs fa;
+    fa.S = c->lv[l].S;
+    fa.M = c->lv[l].M;
+    fa.g = g;
+    fa.alpha2 = c->p.alpha * c->p.alpha;
+    fa.stop_iter = c->ctl + lc;
+    fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms);
+    // L2 prefetch of the bricks of the block one block per SM ahead (a
+    // quarter of a wave of four blocks per SM; measured on 256x256x100
+    // against 2, 3, 4, 6 and 8 blocks per SM ahead and none)
+    fa.pf_stride = c->num_sms;
+    fa.err = c->derr;
+    fa.img_type = c->img_type(l);
+    fa.field_type = c->field_type;
+    return fa;
+}
+
+static dirk::SmoothArgs level_smooth_args(const dir_ctx* c, int lc) {
+    const int l = c->levels - 1 - lc;
+    dirk::SmoothArgs sa;
+    sa.g = c->lv[l].g;
+    sa.ncomp = 3;
+    sa.taps = c->taps;
+    sa.stop_iter = c->ctl + lc;
+    sa.err = c->derr;
+    sa.in_type = c->field_type;
+    sa.out_type = c->field_type;
+    sa.zchunk = c->tune_zchunk[l];
+    return sa;
+}
+
+// The end of every registration: the static-grid field of Eq. 6 for the
+// inverse-consistent law, and where the result lives.
+static int enqueue_epilogue(dir_ctx* c, char* cur, char* oth, cudaStream_t s) {
+    if (c->variant == DIR_INVERSE_CONSISTENT) {
+        CK(c, dirk::launch_ic_invert(c->fp64, c->field_type, cur, oth, c->lv[0].g, kIcInvertSteps, s));
+        c->launches += 1;
+        c->final_field = oth;
+    } else {
+        c->final_field = cur;
+    }
+    return DIR_OK;
+}
+
+static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
+    const int L = c->levels;
+    const bool f64 = c->fp64;
+    const bool plain = c->p.plain_kernels != 0;
+    {
+        const int rc = enqueue_prologue(c, s);
+        if (rc != DIR_OK) return rc;
+    }
     char* cur = c->A;
     char* oth = c->B;
     int row = 0;
@@ -317,45 +401,13 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
     for (int lc = 0; lc < L; ++lc) {
         const int l = L - 1 - lc;
         const Grid3& g = c->lv[l].g;
-        if (lc == 0) {
-            if (c->p.init_field) {
-                const int rc = import_dense(c, c->p.init_field, 1, 4, cur, c->field_type, g, 3, s);
-                if (rc != DIR_OK) return rc;
-                if (c->field_type != dirk::kStoreF32) c->launches += 1;
-            } else {
-                CK(c, cudaMemsetAsync(cur, 0, c->fesz * 3 * (size_t)g.cs, s));
-            }
-        } else {
-            CK(c, dirk::launch_upsample(f64, c->field_type, cur, c->lv[l + 1].g, oth, g, s));
-            c->launches += 1;
-            char* t = cur;
-            cur = oth;
-            oth = t;
+        {
+            const int rc = enqueue_level_start(c, lc, cur, oth, s);
+            if (rc != DIR_OK) return rc;
         }
         c->level_first[lc] = row;
-        dirk::ForceArgs fa;
-        fa.S = c->lv[l].S;
-        fa.M = c->lv[l].M;
-        fa.g = g;
-        fa.alpha2 = c->p.alpha * c->p.alpha;
-        fa.stop_iter = c->ctl + lc;
-        fa.depth = c->tune_depth[l] ? c->tune_depth[l] : dirk::force_brick_depth(g, c->num_sms);
-        // L2 prefetch of the bricks of the block one block per SM ahead (a
-        // quarter of a wave of four blocks per SM; measured on 256x256x100
-        // against 2, 3, 4, 6 and 8 blocks per SM ahead and none)
-        fa.pf_stride = c->num_sms;
-        fa.err = c->derr;
-        fa.img_type = c->img_type(l);
-        fa.field_type = c->field_type;
-        dirk::SmoothArgs sa;
-        sa.g = g;
-        sa.ncomp = 3;
-        sa.taps = c->taps;
-        sa.stop_iter = c->ctl + lc;
-        sa.err = c->derr;
-        sa.in_type = c->field_type;
-        sa.out_type = c->field_type;
-        sa.zchunk = c->tune_zchunk[l];
+        dirk::ForceArgs fa = level_force_args(c, lc);
+        dirk::SmoothArgs sa = level_smooth_args(c, lc);
         const bool timed = c->p.timing && l == 0;
         const int n = c->p.iters[lc];
         const int sched = level_schedule(c, l);
@@ -501,14 +553,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             }
         }
     }
-    if (c->variant == DIR_INVERSE_CONSISTENT) {
-        CK(c, dirk::launch_ic_invert(f64, c->field_type, cur, oth, c->lv[0].g, kIcInvertSteps, s));
-        c->launches += 1;
-        c->final_field = oth;
-    } else {
-        c->final_field = cur;
-    }
-    return DIR_OK;
+    return enqueue_epilogue(c, cur, oth, s);
 }
 
 static int capture_graph(dir_ctx* c) {
@@ -1033,6 +1078,7 @@ struct dir_batch {
     cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
     cudaGraphExec_t exec = nullptr;
     int branches = 1;
+    bool grouped = false;  // grouped launches per iteration (else per-context branches)
 };
 
 static double ctx_work(const dir_ctx* c) {
@@ -1067,8 +1113,155 @@ static void batch_release(dir_batch* b) {
         }                                             \
     } while (0)
 
+// The grouped form's requirements (see dir_batch_create in dir.h)
+static bool batch_groupable(dir_ctx* const* ctxs, int n) {
+    const dir_ctx* c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        const dir_ctx* c = ctxs[i];
+        if (c->fp64 || c->p.plain_kernels || c->field_type != dirk::kStoreF32 ||
+            c->p.stop_mode != 0 || (c->p.fuse != 2 && c->p.fuse != 3) || c->taps.R != 3 ||
+            c->levels != c0->levels || c->taps.wf[0] != c0->taps.wf[0])
+            return false;
+        for (int lc = 0; lc < c->levels; ++lc)
+            if (c->p.iters[lc] != c0->p.iters[lc]) return false;
+        for (int l = 0; l < c->levels; ++l)
+            if (c->img_type(l) != dirk::kStoreF32 && c->img_type(l) != dirk::kStoreI16) return false;
+    }
+    return true;
+}
+
+// Records one chunk of the grouped form on stream s (under capture): jobs of
+// one force law and image storage, at most kGroupMax, moving in lockstep.  Per
+// level: each job's field start and first force pass, then every later
+// iteration as one grouped x/y and one grouped z + force launch over all the
+// jobs, then each job's last smoothing.
+static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& jobs,
+                                 cudaStream_t s) {
+    const int n = (int)jobs.size();
+    const int L = ctxs[jobs[0]]->levels;
+    std::vector<char*> cur(n), oth(n);
+    std::vector<int> row(n, 0);
+    for (int q = 0; q < n; ++q) {
+        dir_ctx* c = ctxs[jobs[q]];
+        const int rc = enqueue_prologue(c, s);
+        if (rc != DIR_OK) return rc;
+        cur[q] = c->A;
+        oth[q] = c->B;
+        c->n_timed = 0;
+    }
+    dir_ctx* c0 = ctxs[jobs[0]];
+    for (int lc = 0; lc < L; ++lc) {
+        const int l = L - 1 - lc;
+        const int iters = c0->p.iters[lc];
+        std::vector<Grid3> grids(n);
+        for (int q = 0; q < n; ++q) {
+            dir_ctx* c = ctxs[jobs[q]];
+            const int rc = enqueue_level_start(c, lc, cur[q], oth[q], s);
+            if (rc != DIR_OK) return rc;
+            c->level_first[lc] = row[q];
+            c->fused_level[lc] = iters > 0 ? 2 : 0;
+            grids[q] = c->lv[l].g;
+        }
+        if (iters == 0) continue;
+        // iteration 0 from the level's starting field, per job
+        for (int q = 0; q < n; ++q) {
+            dir_ctx* c = ctxs[jobs[q]];
+            dirk::ForceArgs fa = level_force_args(c, lc);
+            fa.u = cur[q];
+            fa.v = oth[q];
+            fa.red = c->red + 3 * (size_t)row[q];
+            fa.corr = c->corr ? c->corr + 4 * (size_t)row[q] : nullptr;
+            fa.iter = 0;
+            fa.depth = dirk::force_brick_depth(c->lv[l].g, c->num_sms);
+            CK(c, dirk::launch_force(c->variant, false, fa, s, false));
+            c->launches += 1;
+        }
+        int ty = 0, zc = 0, depth = 0;
+        dirk::group_shapes(c0->variant, grids.data(), n, c0->num_sms, &ty, &zc, &depth);
+        dirk::XYGroup X;
+        dirk::ZSGroup Z;
+        X.ty = ty;
+        X.zchunk = zc;
+        Z.variant = c0->variant;
+        Z.depth = depth;
+        Z.taps = c0->taps;
+        for (int q = 0; q < n; ++q) {
+            dir_ctx* c = ctxs[jobs[q]];
+            dirk::SmoothArgs sa = level_smooth_args(c, lc);
+            sa.in = oth[q];
+            sa.out = cur[q];
+            sa.stop_iter = nullptr;
+            sa.iter = 0;
+            dirk::ForceArgs fa = level_force_args(c, lc);
+            fa.u = cur[q];
+            fa.v = oth[q];
+            fa.stop_iter = nullptr;
+            fa.depth = depth;
+            if (!dirk::xy_group_add(X, sa) || !dirk::zs_group_add(Z, fa)) {
+                c->err = "grouped batch: a tensor map could not be made";
+                return DIR_EINVAL;
+            }
+        }
+        const int img = c0->img_type(l);
+        for (int it = 1; it < iters; ++it) {
+            for (int q = 0; q < n; ++q) {
+                dir_ctx* c = ctxs[jobs[q]];
+                const size_t r = (size_t)(row[q] + it);
+                Z.a[q].red = c->red + 3 * r;
+                Z.a[q].corr = c->corr ? c->corr + 4 * r : nullptr;
+                Z.a[q].iter = it;
+                X.a[q].iter = it;
+                c->launches += 2;
+            }
+            CK(c0, dirk::launch_smooth_xy_grouped(X, s));
+            CK(c0, dirk::launch_force_zs_grouped(c0->variant, img, Z, s));
+        }
+        // u = G v of the last iteration, per job
+        for (int q = 0; q < n; ++q) {
+            dir_ctx* c = ctxs[jobs[q]];
+            dirk::SmoothArgs sa = level_smooth_args(c, lc);
+            sa.in = oth[q];
+            sa.out = cur[q];
+            sa.stop_iter = nullptr;
+            sa.iter = 0;
+            CK(c, dirk::launch_smooth(false, sa, c->num_sms, s, false));
+            c->launches += 1;
+            row[q] += iters;
+        }
+    }
+    for (int q = 0; q < n; ++q) {
+        const int rc = enqueue_epilogue(ctxs[jobs[q]], cur[q], oth[q], s);
+        if (rc != DIR_OK) return rc;
+    }
+    return DIR_OK;
+}
+
+// Chunks of the grouped form: contexts of one force law and level-0 image
+// storage, split into near-equal chunks of at most kGroupMax
+static std::vector<std::vector<int>> grouped_chunks(dir_ctx* const* ctxs, int n) {
+    std::vector<std::vector<int>> out;
+    std::vector<bool> done(n, false);
+    for (int i = 0; i < n; ++i) {
+        if (done[i]) continue;
+        std::vector<int> m;
+        for (int k = i; k < n; ++k)
+            if (!done[k] && ctxs[k]->variant == ctxs[i]->variant &&
+                ctxs[k]->img_type(0) == ctxs[i]->img_type(0)) {
+                m.push_back(k);
+                done[k] = true;
+            }
+        const int parts = ((int)m.size() + dirk::kGroupMax - 1) / dirk::kGroupMax;
+        for (int p = 0; p < parts; ++p) {
+            std::vector<int> chunk;
+            for (int q = p; q < (int)m.size(); q += parts) chunk.push_back(m[q]);
+            out.push_back(chunk);
+        }
+    }
+    return out;
+}
+
 extern "C" int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, int branches,
-                                void* cuda_stream) {
+                                int flags, void* cuda_stream) {
     g_create_error.clear();
     if (!out) return DIR_EINVAL;
     *out = nullptr;
@@ -1088,7 +1281,11 @@ extern "C" int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, in
     if (!b) return DIR_ENOMEM;
     b->ctxs.assign(ctxs, ctxs + n);
     b->stream = (cudaStream_t)cuda_stream;
-    b->branches = branches < n ? branches : n;
+    // grouped form: one branch per chunk; branch form: `branches` (at most n)
+    b->grouped = !(flags & DIR_BATCH_BRANCHES) && batch_groupable(ctxs, n);
+    std::vector<std::vector<int>> chunks;
+    if (b->grouped) chunks = grouped_chunks(ctxs, n);
+    b->branches = b->grouped ? (int)chunks.size() : (branches < n ? branches : n);
     BK(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
     BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     BK(cudaEventCreate(&b->t0));
@@ -1119,17 +1316,36 @@ extern "C" int dir_batch_create(dir_batch** out, dir_ctx* const* ctxs, int n, in
     }
     BK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
     int rc = DIR_OK;
-    cudaError_t ce = cudaEventRecord(b->fork, b->origin);
-    for (int k = 0; k < b->branches && ce == cudaSuccess; ++k)
-        ce = cudaStreamWaitEvent(b->br[k], b->fork, 0);
-    for (int i : order) {
-        if (ce != cudaSuccess || rc != DIR_OK) break;
-        rc = enqueue_registration(ctxs[i], b->br[branch_of[i]], true);
-        if (rc != DIR_OK) g_create_error = ctxs[i]->err;
-    }
-    for (int k = 0; k < b->branches && ce == cudaSuccess; ++k) {
-        ce = cudaEventRecord(b->join[k], b->br[k]);
-        if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    cudaError_t ce = cudaSuccess;
+    if (b->grouped) {
+        // each chunk on its own branch (chunks never share data), in lockstep
+        // within the chunk
+        ce = cudaEventRecord(b->fork, b->origin);
+        for (int k = 0; k < b->branches && ce == cudaSuccess; ++k)
+            ce = cudaStreamWaitEvent(b->br[k], b->fork, 0);
+        for (size_t k = 0; k < chunks.size() && ce == cudaSuccess && rc == DIR_OK; ++k) {
+            rc = enqueue_grouped_chunk(ctxs, chunks[k], b->br[k]);
+            if (rc != DIR_OK)
+                for (int i : chunks[k])
+                    if (!ctxs[i]->err.empty()) g_create_error = ctxs[i]->err;
+        }
+        for (int k = 0; k < b->branches && ce == cudaSuccess; ++k) {
+            ce = cudaEventRecord(b->join[k], b->br[k]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+        }
+    } else {
+        ce = cudaEventRecord(b->fork, b->origin);
+        for (int k = 0; k < b->branches && ce == cudaSuccess; ++k)
+            ce = cudaStreamWaitEvent(b->br[k], b->fork, 0);
+        for (int i : order) {
+            if (ce != cudaSuccess || rc != DIR_OK) break;
+            rc = enqueue_registration(ctxs[i], b->br[branch_of[i]], true);
+            if (rc != DIR_OK) g_create_error = ctxs[i]->err;
+        }
+        for (int k = 0; k < b->branches && ce == cudaSuccess; ++k) {
+            ce = cudaEventRecord(b->join[k], b->br[k]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+        }
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
@@ -1175,6 +1391,8 @@ extern "C" int dir_batch_run(dir_batch* b, float* ms_out) {
     }
     return DIR_OK;
 }
+
+extern "C" int dir_batch_grouped(const dir_batch* b) { return b ? (b->grouped ? 1 : 0) : -1; }
 
 extern "C" void dir_batch_destroy(dir_batch* b) { batch_release(b); }
 

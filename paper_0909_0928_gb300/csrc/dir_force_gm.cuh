@@ -41,7 +41,8 @@ struct FGGeom {
 // Every thread of the block calls it (one barrier inside).
 template <int V, int FTZ, typename TI, int UC>
 __device__ __forceinline__ void gm_force_body(const ForceArgs& a, const float* __restrict__ ub,
-                                              const TI* __restrict__ sb, float* __restrict__ wt) {
+                                              const TI* __restrict__ sb, float* __restrict__ wt,
+                                              const BlockPos bp) {
     using F = FGGeom<FTZ, V, TI>;
     constexpr int FSW = F::FSW, UW = F::UW, UH = F::UH;
     constexpr int HX = F::HX, HY = F::HY, HZ = F::HZ;
@@ -51,7 +52,7 @@ __device__ __forceinline__ void gm_force_body(const ForceArgs& a, const float* _
     float* __restrict__ v = static_cast<float*>(a.v);
     const float alpha2 = (float)a.alpha2;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + FTX * ty;
-    const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
+    const int bx0 = bp.x * FTX, by0 = bp.y * FTY, bz0 = bp.z * FTZ;
     const int ux0 = bx0 - 4, uy0 = by0 - 1, uz0 = bz0 - 1;     // u box origin
     const int sx0 = bx0 - F::FBX, sy0 = by0 - 1, sz0 = bz0 - 1;  // S box origin
     const Interp ip(g);

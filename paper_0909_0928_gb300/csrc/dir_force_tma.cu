@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(FNT, 4)
         return;
     }
     (void)mbar_try_wait(bar, 0);
-    gm_force_body<V, FTZ, TI, F::UD * F::UH * F::UW>(a, ub, sb, wt);
+    gm_force_body<V, FTZ, TI, F::UD * F::UH * F::UW>(a, ub, sb, wt, BlockPos::of_grid());
 }
 
 template <typename TI>

@@ -3,6 +3,7 @@
 // Each launcher returns the cudaError_t of its launch.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -75,6 +76,46 @@ cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
 int force_zs_depth(int variant, const Grid3& g, int num_sms);
 cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
+
+// Grouped launches of the split schedule: one kernel over the blocks of up to
+// kGroupMax volumes (the same pyramid level of several registrations, each
+// with its own tensor maps and arguments), so that the fixed latencies of a
+// launch are paid once for all of them.  Block b of the launch belongs to job
+// j when first[j] <= b < first[j + 1], and is block b - first[j] of that job's
+// own grid (gx x gy x gz, x fastest).  Jobs of one launch share the Gaussian
+// (radius 3), the force law, the image storage and the brick shape.  The
+// structures travel as __grid_constant__ kernel parameters (about 9 KB).
+constexpr int kGroupMax = 16;
+struct XYGroup {
+    CUtensorMap map[kGroupMax];  // each job's plane box of v (x/y kernel layout)
+    SmoothArgs a[kGroupMax];
+    int first[kGroupMax + 1];
+    int gx[kGroupMax], gy[kGroupMax], gz[kGroupMax];
+    int n = 0;                   // jobs
+    int ty = 0;                  // tile rows, 16 or 32 (all jobs)
+    int zchunk = 0;              // planes per block (all jobs)
+};
+struct ZSGroup {
+    CUtensorMap tmap[kGroupMax], smap[kGroupMax], mmap[kGroupMax];
+    ForceArgs a[kGroupMax];
+    int first[kGroupMax + 1];
+    int gx[kGroupMax], gy[kGroupMax], gz[kGroupMax];
+    Taps taps;
+    int n = 0;
+    int variant = 0;             // force law (all jobs)
+    int depth = 0;               // brick depth (all jobs)
+};
+// Shapes for a group of jobs with the given level grids: the x/y kernel's tile
+// rows and z chunk, and the z + force kernel's brick depth (the one-volume
+// rules applied to the group's total block count).
+void group_shapes(int variant, const Grid3* grids, int n, int num_sms, int* ty, int* zchunk,
+                  int* depth);
+// Add a job (its arguments; a.in / a.u its input field) to a group with
+// shapes already set; false if a tensor map cannot be made.
+bool xy_group_add(XYGroup& G, const SmoothArgs& a);
+bool zs_group_add(ZSGroup& G, const ForceArgs& a);
+cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s);
+cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s);
 
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
 // force kernel's work, v = u - dr(u); red as for ForceArgs.

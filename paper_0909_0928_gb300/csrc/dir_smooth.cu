@@ -18,6 +18,7 @@
 #include "dir_common.cuh"
 #include "dir_launch.h"
 #include "dir_smooth2.cuh"
+#include "dir_split.cuh"
 #include "dir_stencil.cuh"
 
 namespace dirk {
@@ -186,90 +187,10 @@ __global__ void __launch_bounds__(8 * TY, 16 / TY * 8)
 // occupancy wants at no extra work, and there is no ring of filtered planes.
 // Same building blocks, layout and order of operations as smooth2_kernel.
 // ---------------------------------------------------------------------------
-constexpr int SXYSTAGES = 4;
-
-template <int R, int TY>
-struct SXYSmem {
-    using G = S2Geom<R, TY>;
-    static constexpr int SMEM = 128 + SXYSTAGES * G::SLOT_STRIDE + G::TXP_STRIDE + 64;
-};
-
 template <int R, int TY>
 __global__ void __launch_bounds__(8 * TY)
     smooth_xy_kernel(const __grid_constant__ CUtensorMap tmap, const SmoothArgs a, int zchunk) {
-    if (a.stop_iter != nullptr && *a.stop_iter < a.iter) return;
-    using G = S2Geom<R, TY>;
-    constexpr int H = G::H, HA = G::HA, WB = G::WB, NT = G::NTG;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    f32x2* txp = reinterpret_cast<f32x2*>(base + SXYSTAGES * G::SLOT_STRIDE);
-    float* txf = reinterpret_cast<float*>(txp);
-    uint64_t* full =
-        reinterpret_cast<uint64_t*>(base + SXYSTAGES * G::SLOT_STRIDE + G::TXP_STRIDE);
-    const Grid3 g = a.g;
-    float w[R + 1];
-    f32x2 wp[R + 1];
-#pragma unroll
-    for (int t = 0; t <= R; ++t) {
-        w[t] = a.taps.wf[t];
-        wp[t] = f2_pack(w[t], w[t]);
-    }
-    const int tid = threadIdx.x;
-    const int lx = tid & 31, q = tid >> 5;
-    const int comp = blockIdx.z % a.ncomp;
-    const int x0 = blockIdx.x * S2X, y0 = blockIdx.y * TY;
-    const int z0 = (blockIdx.z / a.ncomp) * zchunk;
-    const int nsteps = min(z0 + zchunk, g.nz) - z0;  // planes z0 .. z0 + nsteps - 1
-    const int bx = x0 - HA, by = y0 - R;
-    const bool edge = (bx < 0) || (bx + WB > g.nx) || (by < 0) || (by + H > g.ny);
-    float* __restrict__ out = static_cast<float*>(a.out) + (long long)comp * g.cs;
-
-    auto issue = [&](int step) {
-        const int sl = step % SXYSTAGES;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
-        tma_load_4d(base + sl * G::SLOT_STRIDE, &tmap, bx, by, z0 + step, comp, &full[sl]);
-    };
-    if (tid == 0) {
-        for (int sl = 0; sl < SXYSTAGES; ++sl) mbar_init(&full[sl], 1);
-        fence_mbar_init();
-        fence_proxy_async();
-        for (int st = 0; st < SXYSTAGES - 1 && st < nsteps; ++st) issue(st);
-    }
-    __syncthreads();
-
-    const int x = x0 + lx;
-    const int ya = y0 + 2 * q;  // rows ya, ya + 1 (lane 0) and ya + TY/2, ya + TY/2 + 1 (lane 1)
-    const int px = (int)g.px;
-    const int rows_left = x < g.nx ? g.ny - ya : 0;  // 0: this thread stores nothing
-    for (int step = 0; step < nsteps; ++step) {
-        if (tid == 0 && step + SXYSTAGES - 1 < nsteps) issue(step + SXYSTAGES - 1);
-        const int sl = step % SXYSTAGES;
-        const uint32_t parity = (uint32_t)((step / SXYSTAGES) & 1);
-        bool ok = true;
-        if (tid == 0) ok = mbar_wait_bounded(&full[sl], parity, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0 && a.err) atomicOr(a.err, kErrTmaTimeout);
-            return;
-        }
-        (void)mbar_try_wait(&full[sl], parity);
-        float* slot = reinterpret_cast<float*>(base + sl * G::SLOT_STRIDE);  // [H][WB]
-        if (edge) s2_edge_fix<R, TY>(slot, G::SLOT_STRIDE / 4, 1, bx, by, g, tid, NT);
-        s2_xpass<R, TY>(slot, txf, tid, w);
-        __syncthreads();
-        f32x2 r0, r1;
-        s2_y_pair<R>(txp, q, lx, wp, r0, r1);
-        float a0, b0, a1, b1;
-        f2_unpack(r0, a0, b0);
-        f2_unpack(r1, a1, b1);
-        float* o = out + offs(g, x < g.nx ? x : 0, ya, z0 + step);
-        if (rows_left > 0) o[0] = a0;
-        if (rows_left > 1) o[px] = a1;
-        if (rows_left > TY / 2) o[(TY / 2) * px] = b0;
-        if (rows_left > TY / 2 + 1) o[(TY / 2 + 1) * px] = b1;
-        // the next step's __syncthreads_or orders this step's reads of the
-        // pair rows before the next x pass rewrites them
-    }
+    sxy_block<R, TY>(&tmap, a, zchunk, BlockPos::of_grid());
 }
 
 // ---------------------------------------------------------------------------

@@ -2,9 +2,11 @@
 launch-shape autotuner.
 
 A registration's field does not depend on how its kernels are grouped or
-shaped: the batch runs the same kernels as a plain dir_register, only on
-concurrent graph branches, and the autotuner changes only how many voxels a
-thread or block covers, never the arithmetic of a voxel.  So fields are
+shaped: the batch runs the same per-voxel arithmetic as a plain dir_register,
+either as grouped launches over all the pairs of a level (one launch per
+iteration step for the whole batch) or as each registration on concurrent
+graph branches, and the autotuner changes only how many voxels a thread or
+block covers.  So fields are
 compared exactly with plain single registrations, and batched fields are held
 to the FP64 oracle on every voxel (the short schedule keeps the oracle's own
 single-precision sensitivity far below the bar)."""
@@ -67,15 +69,17 @@ def test_batch_equals_plain_registrations(dl):
     ctxs = [_ctx(dl, S, M, v) for (S, M), (_, v, _) in zip(pairs, CASES)]
     batch = None
     try:
-        for branches in (3, 8):
+        for grouped, branches in ((True, 8), (False, 3), (False, 8)):
             batch = dl.dir_batch_create(ctxs, branches=branches,
-                                        stream=torch.cuda.current_stream())
+                                        stream=torch.cuda.current_stream(), grouped=grouped)
+            assert dl.dir_batch_grouped(batch) == grouped
             for rep in range(2):  # a replay gives the same fields again
                 ms = dl.dir_batch_run(batch)
                 assert ms > 0.0
                 for k, ctx in enumerate(ctxs):
                     f = _field(dl, ctx, pairs[k][0].shape)
-                    assert np.array_equal(f, plain[k]), f"pair {k} branches {branches} rep {rep}"
+                    assert np.array_equal(f, plain[k]), (
+                        f"pair {k} grouped {grouped} branches {branches} rep {rep}")
                     h = dl.dir_get_history(ctx, 40)
                     assert h.shape[0] == 40 and np.all(np.isfinite(h[:, 0]))
             dl.dir_batch_destroy(batch)
@@ -91,6 +95,57 @@ def test_batch_equals_plain_registrations(dl):
         # contexts stay usable on their own after the batch is gone
         dl.dir_register(ctxs[0])
         assert np.array_equal(_field(dl, ctxs[0], pairs[0][0].shape), plain[0])
+    finally:
+        dl.dir_batch_destroy(batch)
+        for c in ctxs:
+            dl.dir_destroy(c)
+
+
+def test_grouped_batch_over_many_pairs_and_its_fallback(dl):
+    # 18 pairs of one force law: two launches of at most 16 jobs per step.
+    # The fields agree with plain registrations bit for bit; the histories to
+    # single-precision rounding, because a grouped launch picks one brick
+    # depth for the whole group and so partitions the FP32 per-block partial
+    # sums differently.  A context with a stop test makes the batch fall back
+    # to branches.
+    dims = [(24 + 4 * (k % 5), 20 + 4 * (k % 3), 12 + 2 * (k % 4)) for k in range(18)]
+    pairs = [_pair(100 + k, d, "f32") for k, d in enumerate(dims)]
+    plain, hist = [], []
+    for S, M in pairs:
+        ctx = _ctx(dl, S, M, 0, iters=(6, 4, 3))
+        try:
+            dl.dir_register(ctx)
+            plain.append(_field(dl, ctx, S.shape))
+            hist.append(dl.dir_get_history(ctx, 13))
+        finally:
+            dl.dir_destroy(ctx)
+    ctxs = [_ctx(dl, S, M, 0, iters=(6, 4, 3)) for S, M in pairs]
+    batch = None
+    try:
+        batch = dl.dir_batch_create(ctxs, stream=torch.cuda.current_stream())
+        assert dl.dir_batch_grouped(batch)
+        dl.dir_batch_run(batch)
+        for k, ctx in enumerate(ctxs):
+            assert np.array_equal(_field(dl, ctx, pairs[k][0].shape), plain[k]), f"pair {k}"
+            np.testing.assert_allclose(dl.dir_get_history(ctx, 13), hist[k], rtol=1e-5,
+                                       atol=1e-9)
+        dl.dir_batch_destroy(batch)
+        batch = None
+        S, M = pairs[0]
+        nz, ny, nx = S.shape
+        p = dl.dir_params_default(levels=3, iters=[6, 4, 3], stop_mode=1)
+        odd = dl.dir_create(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (nx, ny, nz),
+                            (1.0, 1.0, 2.0), dl.DIR_F32, True, 0, p, torch.cuda.current_stream())
+        try:
+            batch = dl.dir_batch_create(ctxs[:3] + [odd], stream=torch.cuda.current_stream())
+            assert not dl.dir_batch_grouped(batch)
+            dl.dir_batch_run(batch)
+            for k in range(3):
+                assert np.array_equal(_field(dl, ctxs[k], pairs[k][0].shape), plain[k])
+        finally:
+            dl.dir_batch_destroy(batch)
+            batch = None
+            dl.dir_destroy(odd)
     finally:
         dl.dir_batch_destroy(batch)
         for c in ctxs:
