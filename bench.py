@@ -108,9 +108,10 @@ KERNEL_SOURCES = {
                       "dir_force_law.cuh", "dir_common.cuh"],
     "fused_small_kernel": ["dir_fused.cu", "dir_smooth2.cuh", "dir_force_kernel.cuh",
                            "dir_force_law.cuh", "dir_common.cuh"],
-    "smooth_xy_kernel": ["dir_smooth.cu", "dir_smooth2.cuh", "dir_common.cuh"],
-    "force_zs_kernel": ["dir_force_zs.cu", "dir_force_gm.cuh", "dir_force_kernel.cuh",
-                        "dir_force_law.cuh", "dir_stencil.cuh", "dir_common.cuh"],
+    "smooth_xy_kernel": ["dir_smooth.cu", "dir_split.cuh", "dir_smooth2.cuh", "dir_common.cuh"],
+    "force_zs_kernel": ["dir_force_zs.cu", "dir_split.cuh", "dir_force_gm.cuh",
+                        "dir_force_kernel.cuh", "dir_force_law.cuh", "dir_stencil.cuh",
+                        "dir_common.cuh"],
 }
 
 
