@@ -152,6 +152,38 @@ def test_grouped_batch_over_many_pairs_and_its_fallback(dl):
             dl.dir_destroy(c)
 
 
+def test_grouped_batch_correlation(dl):
+    # the correlation sums of every iteration through the grouped launches:
+    # the plain registration's values (the sums are partitioned differently,
+    # so to single-precision rounding), the fields bit for bit
+    pairs = [_pair(200 + k, (40 + 8 * k, 36, 24), "f32") for k in range(4)]
+    ctxs, plain, rho0 = [], [], []
+    for k, (S, M) in enumerate(pairs):
+        nz, ny, nx = S.shape
+        p = dl.dir_params_default(levels=3, iters=[8, 6, 4], correlation=1)
+        c = dl.dir_create(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (nx, ny, nz),
+                          (1.0, 1.0, 2.0), dl.DIR_F32, True, 5 if k % 2 else 0, p,
+                          torch.cuda.current_stream())
+        ctxs.append(c)
+        dl.dir_register(c)
+        plain.append(_field(dl, c, S.shape))
+        rho0.append(dl.dir_get_correlation(c, 18))
+    batch = None
+    try:
+        batch = dl.dir_batch_create(ctxs, stream=torch.cuda.current_stream())
+        assert dl.dir_batch_grouped(batch)
+        dl.dir_batch_run(batch)
+        for k, c in enumerate(ctxs):
+            assert np.array_equal(_field(dl, c, pairs[k][0].shape), plain[k])
+            rho = dl.dir_get_correlation(c, 18)
+            assert rho.shape == rho0[k].shape == (18,)
+            np.testing.assert_allclose(rho, rho0[k], rtol=0, atol=1e-6)
+    finally:
+        dl.dir_batch_destroy(batch)
+        for c in ctxs:
+            dl.dir_destroy(c)
+
+
 def test_batch_argument_errors(dl):
     S, M = _pair(0, (32, 24, 16), "f32")
     c = _ctx(dl, S, M, 0, iters=(2, 2, 2))
