@@ -347,6 +347,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream serialization attribute may start while the kernel before it in the
+// stream still runs.  pdl_trigger lets the next kernel start; pdl_wait blocks
+// until the kernels this one depends on have completed and their memory is
+// visible.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Position of a block in its own launch grid: the whole launch, or one job's
 // share of a grouped launch over several volumes.
 struct BlockPos {

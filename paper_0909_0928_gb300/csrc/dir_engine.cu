@@ -479,6 +479,17 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             const int zs_depth =
                 c->tune_depth[l] ? c->tune_depth[l] : dirk::force_zs_depth(c->variant, g, c->num_sms);
             const int first_depth = dirk::force_brick_depth(g, c->num_sms);
+            // programmatic dependent launch on mid-size levels (about one wave
+            // of blocks per kernel, so each launch is mostly latency): a
+            // kernel's blocks set up and copy the static images while the one
+            // before finishes.  Measured per level on the 256x256x100 pyramid:
+            // 128x128x50 passive 17.96 -> 16.69 us per iteration, but the
+            // 64x64x25 level slower (7.19 -> 7.28 us; Eq. 6 18.1 -> 19.7), and
+            // on large levels early blocks would hold room the kernel before
+            // still needs.  Not with a stop test (the kernels read the stop flag
+            // before they wait).
+            const long long nvox = (long long)g.nx * g.ny * g.nz;
+            const bool pdl = c->p.stop_mode == 0 && nvox > (1LL << 18) && nvox <= (1LL << 21);
             for (int it = 0; it < n; ++it, ++row) {
                 cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
                 if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -494,11 +505,11 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
                 } else {
                     xa.iter = it;
-                    CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s));
+                    CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s, pdl));
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
                     fa.u = tbuf;
                     fa.depth = zs_depth;
-                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
+                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s, pdl));
                     c->launches += 2;
                 }
                 if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;

@@ -67,7 +67,9 @@ cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStrea
 // three components, radius 1..4): out = G_y * G_x * in.  With
 // launch_force_zs, which applies G_z, one smoothing + force iteration.
 bool smooth_xy_supported(const SmoothArgs& a);
-cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
+// pdl: as a programmatic dependent launch (only without a stop test: the
+// kernels read the stop flag before waiting for the kernel before)
+cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s, bool pdl = false);
 
 // Force pass of Eqs. 1-2 whose u is G_z * t, t = a.u the output of
 // launch_smooth_xy (single-precision field, float or int16 images, radius 3):
@@ -75,7 +77,8 @@ cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
 // launch_smooth + launch_force.  Brick depth a.depth (8, 6, 4, 2 or 1).
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
 int force_zs_depth(int variant, const Grid3& g, int num_sms);
-cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
+cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s,
+                            bool pdl = false);
 
 // Grouped launches of the split schedule: one kernel over the blocks of up to
 // kGroupMax volumes (the same pyramid level of several registrations, each

@@ -5,6 +5,14 @@
 // volumes (dir_grouped.cu).  Each call handles the block at BlockPos bp of its
 // own volume's grid.
 //
+// Launched with programmatic dependent launch (coarse levels, no stop test),
+// a block starts while the kernel before still runs: it sets up its barriers
+// and copies the static images, then waits (pdl_wait) before it reads the
+// field the kernel before wrote or writes one that kernel reads.  The stop
+// flag is read before that wait, which is sound only because such launches
+// are made without a stop test, when the flag does not change during a
+// registration.
+//
 // One iteration of Sec. 2.1 is u = G_sigma * v (Thirion's smoothing of the
 // total field), then v = u - dr(u).  The Gaussian is separable (x, then y,
 // then z), and the Eqs. 1-2 force needs u only at the voxel itself, so the
@@ -73,15 +81,18 @@ __device__ __forceinline__ void zs_block(const CUtensorMap* tmap, const CUtensor
     // x/y pass (bottom up) finds the v this kernel wrote last
     const int bx0 = bp.x * FTX, by0 = bp.y * FTY;
     const int bz0 = (bp.gz - 1 - bp.z) * FTZ;
+    pdl_trigger();
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, (uint32_t)(F::TBOX + F::SBOX + (V == 1 ? F::SBOX : 0)));
-        // planes outside the volume arrive zero-filled; replicated below
-        tma_load_4d(base, tmap, bx0, by0, bz0 - R, 0, bar);
+        // the static images first: they do not depend on the kernel before
         tma_load_4d(base + F::OFF_S, smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
         if (V == 1) tma_load_4d(base + F::OFF_M, mmap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
+        pdl_wait();
+        // planes outside the volume arrive zero-filled; replicated below
+        tma_load_4d(base, tmap, bx0, by0, bz0 - R, 0, bar);
         if (a.pf_stride > 0) {  // the block pf_stride positions ahead: its boxes into L2
             const long long gx = bp.gx, gy = bp.gy;
             const long long b = bp.x + gx * (bp.y + gy * (long long)bp.z) +
@@ -95,6 +106,7 @@ __device__ __forceinline__ void zs_block(const CUtensorMap* tmap, const CUtensor
             }
         }
     }
+    pdl_wait();  // every thread: v is written below, which the kernel before reads
     __syncthreads();
     bool ok = true;
     if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
@@ -233,13 +245,15 @@ __device__ __forceinline__ void gzs_block(const CUtensorMap* tmap, const CUtenso
     const int tid = threadIdx.x + FTX * threadIdx.y;
     const int bx0 = bp.x * FTX, by0 = bp.y * FTY, bz0 = bp.z * FTZ;
     const int zlo = bz0 - 1 - R;  // global plane of box plane 0
+    pdl_trigger();
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, (uint32_t)(Z::TBOX + F::SBOX));
+        tma_load_4d(base + Z::OFF_S, smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);  // static
+        pdl_wait();
         tma_load_4d(base, tmap, bx0 - 4, by0 - 1, zlo, 0, bar);
-        tma_load_4d(base + Z::OFF_S, smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
         if (a.pf_stride > 0) {  // the block pf_stride positions ahead: its boxes into L2
             const long long gx = bp.gx, gy = bp.gy;
             const long long b = bp.x + gx * (bp.y + gy * (long long)bp.z) +
@@ -253,6 +267,7 @@ __device__ __forceinline__ void gzs_block(const CUtensorMap* tmap, const CUtenso
             }
         }
     }
+    pdl_wait();  // every thread: v is written below, which the kernel before reads
     __syncthreads();
     bool ok = true;
     if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
@@ -345,12 +360,15 @@ __device__ __forceinline__ void sxy_block(const CUtensorMap* tmap, const SmoothA
         mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
         tma_load_4d(base + sl * G::SLOT_STRIDE, tmap, bx, by, z0 + step, comp, &full[sl]);
     };
+    pdl_trigger();
     if (tid == 0) {
         for (int sl = 0; sl < SXYSTAGES; ++sl) mbar_init(&full[sl], 1);
         fence_mbar_init();
         fence_proxy_async();
+        pdl_wait();
         for (int st = 0; st < SXYSTAGES - 1 && st < nsteps; ++st) issue(st);
     }
+    pdl_wait();  // every thread: t is written below, which the kernel before reads
     __syncthreads();
 
     const int x = x0 + lx;

@@ -313,6 +313,24 @@ inline cudaError_t setup_kernel(KernelSetup& st, Fn* fn, int smem, int threads =
 // Tensor map of a pitched (x, y, z, component) array of ncomp components with
 // the plane box of StencilGeom<Real, R, NC> (NC components per copy).
 // Returns false if the driver refuses it.
+// Launch a kernel; with pdl, as a programmatic dependent launch (it may start
+// while the kernel before it in the stream still runs; see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*fn)(KArgs...), dim3 grid, dim3 block, int smem,
+                             cudaStream_t s, bool pdl, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<Args&&>(args)...);
+}
+
 template <typename T>
 inline CUtensorMapDataType tma_type();
 template <>
