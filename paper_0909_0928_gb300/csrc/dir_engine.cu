@@ -479,17 +479,16 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             const int zs_depth =
                 c->tune_depth[l] ? c->tune_depth[l] : dirk::force_zs_depth(c->variant, g, c->num_sms);
             const int first_depth = dirk::force_brick_depth(g, c->num_sms);
-            // programmatic dependent launch on mid-size levels (about one wave
-            // of blocks per kernel, so each launch is mostly latency): a
-            // kernel's blocks set up and copy the static images while the one
-            // before finishes.  Measured per level on the 256x256x100 pyramid:
-            // 128x128x50 passive 17.96 -> 16.69 us per iteration, but the
-            // 64x64x25 level slower (7.19 -> 7.28 us; Eq. 6 18.1 -> 19.7), and
-            // on large levels early blocks would hold room the kernel before
-            // still needs.  Not with a stop test (the kernels read the stop flag
-            // before they wait).
+            // programmatic dependent launch above 2^18 voxels: a kernel's blocks
+            // set up and copy the static images while the one before drains
+            // its last wave (they start only once all its blocks have).
+            // Measured per level on the 256x256x100 pyramid: 128x128x50 passive
+            // 17.96 -> 16.7 us per iteration, 256x256x100 94.15 -> 93.48 us
+            // (Eq. 2: 103.8 -> 102.0), but the 64x64x25 level slower (7.19 ->
+            // 7.28 us; Eq. 6 18.1 -> 19.7).  Not with a stop test (the kernels
+            // read the stop flag before they wait).
             const long long nvox = (long long)g.nx * g.ny * g.nz;
-            const bool pdl = c->p.stop_mode == 0 && nvox > (1LL << 18) && nvox <= (1LL << 21);
+            const bool pdl = c->p.stop_mode == 0 && nvox > (1LL << 18);
             for (int it = 0; it < n; ++it, ++row) {
                 cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
                 if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
