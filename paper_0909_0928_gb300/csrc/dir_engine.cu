@@ -241,6 +241,19 @@ static int record(dir_ctx* c, cudaEvent_t e, cudaStream_t s, bool capturing) {
 }
 
 // Issues the whole registration on stream s (captured or direct).
+// Programmatic dependent launch of a level's iteration kernels, above 2^18
+// voxels: a kernel's blocks set up and copy the static images while the one
+// before drains its last wave (they start only once all its blocks have).
+// Measured per level on the 256x256x100 pyramid: 128x128x50 passive 17.96 ->
+// 16.7 us per iteration, 256x256x100 94.15 -> 93.48 us (Eq. 2: 103.8 ->
+// 102.0), but the 64x64x25 level slower (7.19 -> 7.28 us; Eq. 6 18.1 -> 19.7).
+// Not with a stop test (the kernels read the stop flag before they wait), nor
+// with timing events between the kernels.
+static bool level_pdl(const dir_ctx* c, const Grid3& g, bool timed) {
+    return c->p.stop_mode == 0 && !timed && !c->fp64 && !c->p.plain_kernels &&
+           (long long)g.nx * g.ny * g.nz > (1LL << 18);
+}
+
 // Iteration schedule of pyramid level l: 0 force + smoothing kernels, 1 fused
 // iteration (the Gaussian of v_{k-1} folded into the force pass), 2 split
 // Gaussian (its x and y passes as their own kernel, its z pass inside the
@@ -479,16 +492,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             const int zs_depth =
                 c->tune_depth[l] ? c->tune_depth[l] : dirk::force_zs_depth(c->variant, g, c->num_sms);
             const int first_depth = dirk::force_brick_depth(g, c->num_sms);
-            // programmatic dependent launch above 2^18 voxels: a kernel's blocks
-            // set up and copy the static images while the one before drains
-            // its last wave (they start only once all its blocks have).
-            // Measured per level on the 256x256x100 pyramid: 128x128x50 passive
-            // 17.96 -> 16.7 us per iteration, 256x256x100 94.15 -> 93.48 us
-            // (Eq. 2: 103.8 -> 102.0), but the 64x64x25 level slower (7.19 ->
-            // 7.28 us; Eq. 6 18.1 -> 19.7).  Not with a stop test (the kernels
-            // read the stop flag before they wait).
-            const long long nvox = (long long)g.nx * g.ny * g.nz;
-            const bool pdl = c->p.stop_mode == 0 && nvox > (1LL << 18);
+            const bool pdl = level_pdl(c, g, timed);
             for (int it = 0; it < n; ++it, ++row) {
                 cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
                 if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -504,11 +508,13 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
                 } else {
                     xa.iter = it;
-                    CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s, pdl));
+                    xa.pdl = pdl;
+                    CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s));
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
                     fa.u = tbuf;
                     fa.depth = zs_depth;
-                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s, pdl));
+                    fa.pdl = pdl;
+                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
                     c->launches += 2;
                 }
                 if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -533,6 +539,9 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             continue;
         }
         c->fused_level[lc] = 0;
+        // iterations > 0 may start early (level_pdl); iteration 0 follows the
+        // upsampling, which is not written for it
+        const bool pdl2 = level_pdl(c, g, timed);
         for (int it = 0; it < n; ++it, ++row) {
             cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
             if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -541,6 +550,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             fa.red = c->red + 3 * (size_t)row;
             fa.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
             fa.iter = it;
+            fa.pdl = pdl2 && it > 0;
             CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
             c->launches += 1;
             if (c->p.stop_mode >= 1) {
@@ -555,6 +565,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.in = oth;
             sa.out = cur;
             sa.iter = it;
+            sa.pdl = pdl2;
             CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
             c->launches += 1;
             if (timed) {

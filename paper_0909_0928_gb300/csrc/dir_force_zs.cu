@@ -51,7 +51,7 @@ static bool make_zs_maps(CUtensorMap* tmap, CUtensorMap* smap, CUtensorMap* mmap
 }
 
 template <int V, int FTZ, typename TI>
-static cudaError_t launch_zs(const ForceArgs& a, const Taps& taps, cudaStream_t s, bool pdl) {
+static cudaError_t launch_zs(const ForceArgs& a, const Taps& taps, cudaStream_t s) {
     using F = FZGeom<FTZ, V, TI>;
     CUtensorMap tmap, smap, mmap;
     if (!make_zs_maps<TI>(&tmap, &smap, &mmap, a, FTZ)) return cudaErrorInvalidValue;
@@ -59,25 +59,25 @@ static cudaError_t launch_zs(const ForceArgs& a, const Taps& taps, cudaStream_t 
     const cudaError_t e = setup_kernel(setup, force_zs_kernel<V, FTZ, TI>, F::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
-    return launch_ex(force_zs_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), F::SMEM, s, pdl, tmap,
+    return launch_ex(force_zs_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), F::SMEM, s, a.pdl, tmap,
                      smap, mmap, a, taps);
 }
 
 template <typename TI>
 static cudaError_t launch_zs_types(int variant, const ForceArgs& a, const Taps& taps,
-                                   cudaStream_t s, bool pdl) {
+                                   cudaStream_t s) {
     switch (a.depth) {
-        case 8: return variant ? launch_zs<1, 8, TI>(a, taps, s, pdl) : launch_zs<0, 8, TI>(a, taps, s, pdl);
-        case 6: return variant ? launch_zs<1, 6, TI>(a, taps, s, pdl) : launch_zs<0, 6, TI>(a, taps, s, pdl);
-        case 4: return variant ? launch_zs<1, 4, TI>(a, taps, s, pdl) : launch_zs<0, 4, TI>(a, taps, s, pdl);
-        case 2: return variant ? launch_zs<1, 2, TI>(a, taps, s, pdl) : launch_zs<0, 2, TI>(a, taps, s, pdl);
-        case 1: return variant ? launch_zs<1, 1, TI>(a, taps, s, pdl) : launch_zs<0, 1, TI>(a, taps, s, pdl);
+        case 8: return variant ? launch_zs<1, 8, TI>(a, taps, s) : launch_zs<0, 8, TI>(a, taps, s);
+        case 6: return variant ? launch_zs<1, 6, TI>(a, taps, s) : launch_zs<0, 6, TI>(a, taps, s);
+        case 4: return variant ? launch_zs<1, 4, TI>(a, taps, s) : launch_zs<0, 4, TI>(a, taps, s);
+        case 2: return variant ? launch_zs<1, 2, TI>(a, taps, s) : launch_zs<0, 2, TI>(a, taps, s);
+        case 1: return variant ? launch_zs<1, 1, TI>(a, taps, s) : launch_zs<0, 1, TI>(a, taps, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int V, int FTZ, typename TI>
-static cudaError_t launch_gzs(const ForceArgs& a, const Taps& taps, cudaStream_t s, bool pdl) {
+static cudaError_t launch_gzs(const ForceArgs& a, const Taps& taps, cudaStream_t s) {
     using F = FGGeom<FTZ, V, TI>;
     using Z = GZGeom<FTZ, V, TI>;
     EncodeTiledFn enc = encode_fn();
@@ -107,31 +107,30 @@ static cudaError_t launch_gzs(const ForceArgs& a, const Taps& taps, cudaStream_t
     const cudaError_t e = setup_kernel(setup, force_gzs_kernel<V, FTZ, TI>, Z::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((g.nx + FTX - 1) / FTX, (g.ny + FTY - 1) / FTY, (g.nz + FTZ - 1) / FTZ);
-    return launch_ex(force_gzs_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), Z::SMEM, s, pdl, tmap,
+    return launch_ex(force_gzs_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), Z::SMEM, s, a.pdl, tmap,
                      smap, mmap, a, taps);
 }
 
 template <int V, typename TI>
-static cudaError_t launch_gzs_depth(const ForceArgs& a, const Taps& taps, cudaStream_t s,
-                                    bool pdl) {
+static cudaError_t launch_gzs_depth(const ForceArgs& a, const Taps& taps, cudaStream_t s) {
     switch (a.depth) {
         case 8:
         case 6:
-        case 4: return launch_gzs<V, 4, TI>(a, taps, s, pdl);  // at most 4 deep, as force_tma_gm_kernel
-        case 2: return launch_gzs<V, 2, TI>(a, taps, s, pdl);
-        case 1: return launch_gzs<V, 1, TI>(a, taps, s, pdl);
+        case 4: return launch_gzs<V, 4, TI>(a, taps, s);  // at most 4 deep, as force_tma_gm_kernel
+        case 2: return launch_gzs<V, 2, TI>(a, taps, s);
+        case 1: return launch_gzs<V, 1, TI>(a, taps, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename TI>
 static cudaError_t launch_gzs_types(int variant, const ForceArgs& a, const Taps& taps,
-                                    cudaStream_t s, bool pdl) {
+                                    cudaStream_t s) {
     switch (variant) {
-        case 2: return launch_gzs_depth<2, TI>(a, taps, s, pdl);
-        case 3: return launch_gzs_depth<3, TI>(a, taps, s, pdl);
-        case 4: return launch_gzs_depth<4, TI>(a, taps, s, pdl);
-        case 5: return launch_gzs_depth<5, TI>(a, taps, s, pdl);
+        case 2: return launch_gzs_depth<2, TI>(a, taps, s);
+        case 3: return launch_gzs_depth<3, TI>(a, taps, s);
+        case 4: return launch_gzs_depth<4, TI>(a, taps, s);
+        case 5: return launch_gzs_depth<5, TI>(a, taps, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -152,15 +151,14 @@ bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps) {
            (a.img_type == kStoreF32 || a.img_type == kStoreI16) && taps.R == FZR;
 }
 
-cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s,
-                            bool pdl) {
+cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s) {
     if (!force_zs_supported(variant, a, taps)) return cudaErrorInvalidValue;
     if (variant >= 2) {
-        if (a.img_type == kStoreF32) return launch_gzs_types<float>(variant, a, taps, s, pdl);
-        return launch_gzs_types<int16_t>(variant, a, taps, s, pdl);
+        if (a.img_type == kStoreF32) return launch_gzs_types<float>(variant, a, taps, s);
+        return launch_gzs_types<int16_t>(variant, a, taps, s);
     }
-    if (a.img_type == kStoreF32) return launch_zs_types<float>(variant, a, taps, s, pdl);
-    return launch_zs_types<int16_t>(variant, a, taps, s, pdl);
+    if (a.img_type == kStoreF32) return launch_zs_types<float>(variant, a, taps, s);
+    return launch_zs_types<int16_t>(variant, a, taps, s);
 }
 
 }  // namespace dirk

@@ -36,6 +36,9 @@ struct ForceArgs {
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
     double* corr = nullptr;  // non-null: += {Sum b, Sum b^2, Sum d, Sum b d} of the
                              // correlation of the warped image with its reference
+    bool pdl = false;        // launch as a programmatic dependent launch (TMA-fed and
+                             // split kernels; only without a stop test: they read the
+                             // stop flag before waiting for the kernel before)
 };
 // plain = true: the plain-load force_kernel even where a TMA-fed kernel exists
 // (the same per-voxel arithmetic without the tiling; a cross-check of it)
@@ -57,6 +60,7 @@ struct SmoothArgs {
     int in_type;         // storage of in (kStore*)
     int out_type;        // storage of out
     int zchunk;          // planes per block; 0 = one wave of resident blocks
+    bool pdl = false;    // as ForceArgs::pdl (packed and x/y kernels)
 };
 // plain = true: the 32 x 8 tile kernel (smooth_kernel) for every storage type
 // instead of the packed single-precision kernels
@@ -67,9 +71,7 @@ cudaError_t launch_smooth(bool fp64, const SmoothArgs& a, int num_sms, cudaStrea
 // three components, radius 1..4): out = G_y * G_x * in.  With
 // launch_force_zs, which applies G_z, one smoothing + force iteration.
 bool smooth_xy_supported(const SmoothArgs& a);
-// pdl: as a programmatic dependent launch (only without a stop test: the
-// kernels read the stop flag before waiting for the kernel before)
-cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s, bool pdl = false);
+cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
 
 // Force pass of Eqs. 1-2 whose u is G_z * t, t = a.u the output of
 // launch_smooth_xy (single-precision field, float or int16 images, radius 3):
@@ -77,8 +79,7 @@ cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s, b
 // launch_smooth + launch_force.  Brick depth a.depth (8, 6, 4, 2 or 1).
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
 int force_zs_depth(int variant, const Grid3& g, int num_sms);
-cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s,
-                            bool pdl = false);
+cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
 
 // Grouped launches of the split schedule: one kernel over the blocks of up to
 // kGroupMax volumes (the same pyramid level of several registrations, each

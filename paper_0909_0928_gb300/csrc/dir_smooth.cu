@@ -127,12 +127,15 @@ __global__ void __launch_bounds__(8 * TY, 16 / TY * 8)
         mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
         tma_load_4d(base + sl * G::SLOT_STRIDE, &tmap, bx, by, pc, comp, &full[sl]);
     };
+    pdl_trigger();
     if (tid == 0) {
         for (int sl = 0; sl < S2STAGES; ++sl) mbar_init(&full[sl], 1);
         fence_mbar_init();
         fence_proxy_async();
+        pdl_wait();
         for (int st = 0; st < S2STAGES - 1 && st < nsteps; ++st) issue(st);
     }
+    pdl_wait();  // every thread: u is written below, which the kernel before reads
     __syncthreads();
 
     f32x2 ring[K][2];
@@ -382,8 +385,8 @@ static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
     const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + TY - 1) / TY, chunks * a.ncomp);
-    smooth2_kernel<R, TY><<<grid, dim3(8 * TY, 1, 1), G::SMEM, s>>>(map, a, zc);
-    return cudaGetLastError();
+    return launch_ex(smooth2_kernel<R, TY>, grid, dim3(8 * TY, 1, 1), G::SMEM, s, a.pdl, map, a,
+                     zc);
 }
 
 // tile height: 32 rows where the level is large enough that fewer, taller
@@ -396,7 +399,7 @@ static cudaError_t launch_s2t(const SmoothArgs& a, int num_sms, cudaStream_t s) 
 }
 
 template <int R, int TY>
-static cudaError_t launch_sxy(const SmoothArgs& a, int num_sms, cudaStream_t s, bool pdl) {
+static cudaError_t launch_sxy(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     using G = SXYSmem<R, TY>;
     CUtensorMap map;
     if (!make_s2_map<R, TY>(&map, a.in, a.g, a.ncomp)) return cudaErrorInvalidValue;
@@ -422,7 +425,7 @@ static cudaError_t launch_sxy(const SmoothArgs& a, int num_sms, cudaStream_t s, 
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
     const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + TY - 1) / TY, chunks * a.ncomp);
-    return launch_ex(smooth_xy_kernel<R, TY>, grid, dim3(8 * TY, 1, 1), G::SMEM, s, pdl, map, a, zc);
+    return launch_ex(smooth_xy_kernel<R, TY>, grid, dim3(8 * TY, 1, 1), G::SMEM, s, a.pdl, map, a, zc);
 }
 
 template <typename Real, int R, typename TIN, typename TOUT>
@@ -463,15 +466,15 @@ bool smooth_xy_supported(const SmoothArgs& a) {
            a.taps.R <= 4;
 }
 
-cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s, bool pdl) {
+cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     if (!smooth_xy_supported(a)) return cudaErrorInvalidValue;
     const long long tiles32 = (long long)((a.g.nx + S2X - 1) / S2X) * ((a.g.ny + 31) / 32) * a.ncomp;
     const bool tall = tiles32 * a.g.nz >= 8LL * num_sms;
     switch (a.taps.R) {
-        case 1: return tall ? launch_sxy<1, 32>(a, num_sms, s, pdl) : launch_sxy<1, S2Y>(a, num_sms, s, pdl);
-        case 2: return tall ? launch_sxy<2, 32>(a, num_sms, s, pdl) : launch_sxy<2, S2Y>(a, num_sms, s, pdl);
-        case 3: return tall ? launch_sxy<3, 32>(a, num_sms, s, pdl) : launch_sxy<3, S2Y>(a, num_sms, s, pdl);
-        case 4: return tall ? launch_sxy<4, 32>(a, num_sms, s, pdl) : launch_sxy<4, S2Y>(a, num_sms, s, pdl);
+        case 1: return tall ? launch_sxy<1, 32>(a, num_sms, s) : launch_sxy<1, S2Y>(a, num_sms, s);
+        case 2: return tall ? launch_sxy<2, 32>(a, num_sms, s) : launch_sxy<2, S2Y>(a, num_sms, s);
+        case 3: return tall ? launch_sxy<3, 32>(a, num_sms, s) : launch_sxy<3, S2Y>(a, num_sms, s);
+        case 4: return tall ? launch_sxy<4, 32>(a, num_sms, s) : launch_sxy<4, S2Y>(a, num_sms, s);
         default: return cudaErrorInvalidValue;
     }
 }
