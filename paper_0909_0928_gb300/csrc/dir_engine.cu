@@ -1224,6 +1224,9 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
             }
         }
         const int img = c0->img_type(l);
+        long long chunk_vox = 0;  // the level of the whole chunk, for the rule of level_pdl
+        for (int q = 0; q < n; ++q) chunk_vox += (long long)grids[q].nx * grids[q].ny * grids[q].nz;
+        const bool pdl = chunk_vox > (1LL << 18);
         for (int it = 1; it < iters; ++it) {
             for (int q = 0; q < n; ++q) {
                 dir_ctx* c = ctxs[jobs[q]];
@@ -1234,8 +1237,8 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
                 X.a[q].iter = it;
                 c->launches += 2;
             }
-            CK(c0, dirk::launch_smooth_xy_grouped(X, s));
-            CK(c0, dirk::launch_force_zs_grouped(c0->variant, img, Z, s));
+            CK(c0, dirk::launch_smooth_xy_grouped(X, s, pdl));
+            CK(c0, dirk::launch_force_zs_grouped(c0->variant, img, Z, s, pdl));
         }
         // u = G v of the last iteration, per job
         for (int q = 0; q < n; ++q) {

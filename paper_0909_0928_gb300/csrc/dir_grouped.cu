@@ -163,74 +163,73 @@ bool zs_group_add(ZSGroup& G, const ForceArgs& a) {
     return true;
 }
 
-cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s) {
+cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s, bool pdl) {
     if (G.n < 1 || G.first[G.n] < 1) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)G.first[G.n]);
     if (G.ty == 32) {
         static KernelSetup st;
         const cudaError_t e = setup_kernel(st, smooth_xy_grouped_kernel<32>, sxy_smem(32));
         if (e != cudaSuccess) return e;
-        smooth_xy_grouped_kernel<32><<<grid, dim3(8 * 32), sxy_smem(32), s>>>(G);
+        return launch_ex(smooth_xy_grouped_kernel<32>, grid, dim3(8 * 32), sxy_smem(32), s, pdl, G);
     } else if (G.ty == S2Y) {
         static KernelSetup st;
         const cudaError_t e = setup_kernel(st, smooth_xy_grouped_kernel<S2Y>, sxy_smem(S2Y));
         if (e != cudaSuccess) return e;
-        smooth_xy_grouped_kernel<S2Y><<<grid, dim3(8 * S2Y), sxy_smem(S2Y), s>>>(G);
-    } else {
-        return cudaErrorInvalidValue;
+        return launch_ex(smooth_xy_grouped_kernel<S2Y>, grid, dim3(8 * S2Y), sxy_smem(S2Y), s, pdl,
+                         G);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <int V, int FTZ, typename TI>
-static cudaError_t launch_zsg(const ZSGroup& G, cudaStream_t s) {
+static cudaError_t launch_zsg(const ZSGroup& G, cudaStream_t s, bool pdl) {
     constexpr int SMEM = V <= 1 ? FZGeom<FTZ, V, TI>::SMEM : GZGeom<FTZ, V, TI>::SMEM;
     static KernelSetup st;  // per instantiation
     const cudaError_t e = setup_kernel(st, force_zs_grouped_kernel<V, FTZ, TI>, SMEM);
     if (e != cudaSuccess) return e;
-    force_zs_grouped_kernel<V, FTZ, TI>
-        <<<dim3((unsigned)G.first[G.n]), dim3(FTX, FTY, 1), SMEM, s>>>(G);
-    return cudaGetLastError();
+    return launch_ex(force_zs_grouped_kernel<V, FTZ, TI>, dim3((unsigned)G.first[G.n]),
+                     dim3(FTX, FTY, 1), SMEM, s, pdl, G);
 }
 
 template <int V, typename TI>
-static cudaError_t launch_zsg_depth(const ZSGroup& G, cudaStream_t s) {
+static cudaError_t launch_zsg_depth(const ZSGroup& G, cudaStream_t s, bool pdl) {
     if constexpr (V <= 1) {
         switch (G.depth) {
-            case 8: return launch_zsg<V, 8, TI>(G, s);
-            case 6: return launch_zsg<V, 6, TI>(G, s);
-            case 4: return launch_zsg<V, 4, TI>(G, s);
-            case 2: return launch_zsg<V, 2, TI>(G, s);
-            case 1: return launch_zsg<V, 1, TI>(G, s);
+            case 8: return launch_zsg<V, 8, TI>(G, s, pdl);
+            case 6: return launch_zsg<V, 6, TI>(G, s, pdl);
+            case 4: return launch_zsg<V, 4, TI>(G, s, pdl);
+            case 2: return launch_zsg<V, 2, TI>(G, s, pdl);
+            case 1: return launch_zsg<V, 1, TI>(G, s, pdl);
             default: return cudaErrorInvalidValue;
         }
     } else {
         switch (G.depth) {
-            case 4: return launch_zsg<V, 4, TI>(G, s);
-            case 2: return launch_zsg<V, 2, TI>(G, s);
-            case 1: return launch_zsg<V, 1, TI>(G, s);
+            case 4: return launch_zsg<V, 4, TI>(G, s, pdl);
+            case 2: return launch_zsg<V, 2, TI>(G, s, pdl);
+            case 1: return launch_zsg<V, 1, TI>(G, s, pdl);
             default: return cudaErrorInvalidValue;
         }
     }
 }
 
 template <typename TI>
-static cudaError_t launch_zsg_types(int variant, const ZSGroup& G, cudaStream_t s) {
+static cudaError_t launch_zsg_types(int variant, const ZSGroup& G, cudaStream_t s, bool pdl) {
     switch (variant) {
-        case 0: return launch_zsg_depth<0, TI>(G, s);
-        case 1: return launch_zsg_depth<1, TI>(G, s);
-        case 2: return launch_zsg_depth<2, TI>(G, s);
-        case 3: return launch_zsg_depth<3, TI>(G, s);
-        case 4: return launch_zsg_depth<4, TI>(G, s);
-        case 5: return launch_zsg_depth<5, TI>(G, s);
+        case 0: return launch_zsg_depth<0, TI>(G, s, pdl);
+        case 1: return launch_zsg_depth<1, TI>(G, s, pdl);
+        case 2: return launch_zsg_depth<2, TI>(G, s, pdl);
+        case 3: return launch_zsg_depth<3, TI>(G, s, pdl);
+        case 4: return launch_zsg_depth<4, TI>(G, s, pdl);
+        case 5: return launch_zsg_depth<5, TI>(G, s, pdl);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s) {
+cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s,
+                                    bool pdl) {
     if (G.n < 1 || G.first[G.n] < 1 || variant != G.variant) return cudaErrorInvalidValue;
-    if (img_type == kStoreF32) return launch_zsg_types<float>(variant, G, s);
-    if (img_type == kStoreI16) return launch_zsg_types<int16_t>(variant, G, s);
+    if (img_type == kStoreF32) return launch_zsg_types<float>(variant, G, s, pdl);
+    if (img_type == kStoreI16) return launch_zsg_types<int16_t>(variant, G, s, pdl);
     return cudaErrorInvalidValue;
 }
 

@@ -118,8 +118,11 @@ void group_shapes(int variant, const Grid3* grids, int n, int num_sms, int* ty, 
 // shapes already set; false if a tensor map cannot be made.
 bool xy_group_add(XYGroup& G, const SmoothArgs& a);
 bool zs_group_add(ZSGroup& G, const ForceArgs& a);
-cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s);
-cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s);
+// pdl: as programmatic dependent launches (the kernels wait for the one
+// before them before they touch a field; no stop test in a grouped batch)
+cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s, bool pdl = false);
+cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s,
+                                    bool pdl = false);
 
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
 // force kernel's work, v = u - dr(u); red as for ForceArgs.
