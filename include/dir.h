@@ -129,6 +129,10 @@ typedef struct {
                                     of the two warped images) with reductions fused into the
                                     force pass (Secs. 2.4, 3.3; dir_get_correlation); 0
                                     (default): not recorded */
+    int pdl;                     /* 1 (default): on levels above 2^18 voxels without a stop test,
+                                    launch the iteration kernels as programmatic dependent
+                                    launches (each starts its setup while the one before
+                                    drains); 0: plain launches.  The same field either way */
 } dir_params;
 
 typedef struct {

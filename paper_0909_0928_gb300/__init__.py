@@ -48,7 +48,7 @@ class DirParams(C.Structure):
                 ("stop_window", C.c_int), ("field_dtype", C.c_int),
                 ("init_field", C.c_void_p), ("use_graph", C.c_int), ("timing", C.c_int),
                 ("precision", C.c_int), ("fuse", C.c_int), ("plain_kernels", C.c_int),
-                ("correlation", C.c_int)]
+                ("correlation", C.c_int), ("pdl", C.c_int)]
 
 
 class DirStats(C.Structure):

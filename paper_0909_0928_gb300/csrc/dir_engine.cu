@@ -248,9 +248,11 @@ static int record(dir_ctx* c, cudaEvent_t e, cudaStream_t s, bool capturing) {
 // 16.7 us per iteration, 256x256x100 94.15 -> 93.48 us (Eq. 2: 103.8 ->
 // 102.0), but the 64x64x25 level slower (7.19 -> 7.28 us; Eq. 6 18.1 -> 19.7).
 // Not with a stop test (the kernels read the stop flag before they wait), nor
-// with timing events between the kernels.
+// with timing events between the kernels.  Split schedule only: the same
+// launches made the force + smoothing kernels slower (Eq. 3: 13.20 -> 13.35 ms
+// per registration, Eq. 6: 17.07 -> 17.27; split passive 8.20 -> 8.04).
 static bool level_pdl(const dir_ctx* c, const Grid3& g, bool timed) {
-    return c->p.stop_mode == 0 && !timed && !c->fp64 && !c->p.plain_kernels &&
+    return c->p.pdl && c->p.stop_mode == 0 && !timed && !c->fp64 && !c->p.plain_kernels &&
            (long long)g.nx * g.ny * g.nz > (1LL << 18);
 }
 
@@ -539,9 +541,6 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             continue;
         }
         c->fused_level[lc] = 0;
-        // iterations > 0 may start early (level_pdl); iteration 0 follows the
-        // upsampling, which is not written for it
-        const bool pdl2 = level_pdl(c, g, timed);
         for (int it = 0; it < n; ++it, ++row) {
             cudaEvent_t* e = timed ? &c->tev[3 * (size_t)c->n_timed] : nullptr;
             if (timed && record(c, e[0], s, capturing) != DIR_OK) return DIR_ECUDA;
@@ -550,7 +549,6 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             fa.red = c->red + 3 * (size_t)row;
             fa.corr = c->corr ? c->corr + 4 * (size_t)row : nullptr;
             fa.iter = it;
-            fa.pdl = pdl2 && it > 0;
             CK(c, dirk::launch_force(c->variant, f64, fa, s, plain));
             c->launches += 1;
             if (c->p.stop_mode >= 1) {
@@ -565,7 +563,6 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             sa.in = oth;
             sa.out = cur;
             sa.iter = it;
-            sa.pdl = pdl2;
             CK(c, dirk::launch_smooth(f64, sa, c->num_sms, s, plain));
             c->launches += 1;
             if (timed) {
@@ -626,6 +623,7 @@ static int validate_params(const dir_params* p) {
     if (p->stop_mode < 0 || p->stop_mode > 2) return DIR_EINVAL;
     if (p->stop_mode >= 1 && (p->stop_window < 1 || !(p->eps >= 0.0))) return DIR_EINVAL;
     if (p->correlation != 0 && p->correlation != 1) return DIR_EINVAL;
+    if (p->pdl != 0 && p->pdl != 1) return DIR_EINVAL;
     if (p->precision != DIR_F32 && p->precision != DIR_F64) return DIR_EUNSUPPORTED;
     if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
@@ -672,6 +670,7 @@ int dir_params_default(dir_params* p) {
     p->fuse = 2;
     p->plain_kernels = 0;
     p->correlation = 0;
+    p->pdl = 1;
     return DIR_OK;
 }
 
@@ -1226,7 +1225,7 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
         const int img = c0->img_type(l);
         long long chunk_vox = 0;  // the level of the whole chunk, for the rule of level_pdl
         for (int q = 0; q < n; ++q) chunk_vox += (long long)grids[q].nx * grids[q].ny * grids[q].nz;
-        const bool pdl = chunk_vox > (1LL << 18);
+        const bool pdl = c0->p.pdl && chunk_vox > (1LL << 18);
         for (int it = 1; it < iters; ++it) {
             for (int q = 0; q < n; ++q) {
                 dir_ctx* c = ctxs[jobs[q]];

@@ -55,17 +55,14 @@ __global__ void __launch_bounds__(FNT, 4)
     float* __restrict__ v = static_cast<float*>(a.v);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + FTX * ty;
     const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
-    pdl_trigger();
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, (uint32_t)(F::UBOX + F::SBOX + (V == 1 ? F::SBOX : 0)));
-        // static images first, then (pdl_wait) the field the kernel before wrote
+        tma_load_4d(base, &umap, bx0, by0, bz0, 0, bar);
         tma_load_4d(base + F::OFF_S, &smap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
         if (V == 1) tma_load_4d(base + F::OFF_M, &mmap, bx0 - FBX, by0 - 1, bz0 - 1, 0, bar);
-        pdl_wait();
-        tma_load_4d(base, &umap, bx0, by0, bz0, 0, bar);
         // the block pf_stride positions ahead: its bricks into L2
         if (a.pf_stride > 0) {
             const long long gx = gridDim.x, gy = gridDim.y;
@@ -80,7 +77,6 @@ __global__ void __launch_bounds__(FNT, 4)
             }
         }
     }
-    pdl_wait();  // every thread: v is written below, which the kernel before reads
     __syncthreads();
     bool ok = true;
     if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
@@ -187,8 +183,8 @@ static cudaError_t launch_ft(const ForceArgs& a, cudaStream_t s) {
     const cudaError_t e = setup_kernel(setup, force_tma_kernel<V, FTZ, TI>, F::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
-    return launch_ex(force_tma_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), F::SMEM, s, a.pdl, umap,
-                     smap, mmap, a);
+    force_tma_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), F::SMEM, s>>>(umap, smap, mmap, a);
+    return cudaGetLastError();
 }
 
 
@@ -219,15 +215,13 @@ __global__ void __launch_bounds__(FNT, 4)
     const int bx0 = blockIdx.x * FTX, by0 = blockIdx.y * FTY, bz0 = blockIdx.z * FTZ;
     const int ux0 = bx0 - 4, uy0 = by0 - 1, uz0 = bz0 - 1;     // u box origin
     const int sx0 = bx0 - FBX, sy0 = by0 - 1, sz0 = bz0 - 1;   // S box origin
-    pdl_trigger();
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, (uint32_t)(F::UBOX + F::SBOX));
-        tma_load_4d(base + F::OFF_S, &smap, sx0, sy0, sz0, 0, bar);  // static
-        pdl_wait();
         tma_load_4d(base, &umap, ux0, uy0, uz0, 0, bar);
+        tma_load_4d(base + F::OFF_S, &smap, sx0, sy0, sz0, 0, bar);
         if (a.pf_stride > 0) {  // the block pf_stride positions ahead: its boxes into L2
             const long long gx = gridDim.x, gy = gridDim.y;
             const long long b = blockIdx.x + gx * (blockIdx.y + gy * (long long)blockIdx.z) +
@@ -241,7 +235,6 @@ __global__ void __launch_bounds__(FNT, 4)
             }
         }
     }
-    pdl_wait();  // every thread: v is written below, which the kernel before reads
     __syncthreads();
     bool ok = true;
     if (tid == 0) ok = mbar_wait_bounded(bar, 0, kWaitLimitNs);
@@ -290,8 +283,8 @@ static cudaError_t launch_fg(const ForceArgs& a, cudaStream_t s) {
     const cudaError_t e = setup_kernel(setup, force_tma_gm_kernel<V, FTZ, TI>, F::SMEM);
     if (e != cudaSuccess) return e;
     const dim3 grid((a.g.nx + FTX - 1) / FTX, (a.g.ny + FTY - 1) / FTY, (a.g.nz + FTZ - 1) / FTZ);
-    return launch_ex(force_tma_gm_kernel<V, FTZ, TI>, grid, dim3(FTX, FTY, 1), F::SMEM, s, a.pdl,
-                     umap, smap, mmap, a);
+    force_tma_gm_kernel<V, FTZ, TI><<<grid, dim3(FTX, FTY, 1), F::SMEM, s>>>(umap, smap, mmap, a);
+    return cudaGetLastError();
 }
 
 template <int V, typename TI>

@@ -36,8 +36,8 @@ struct ForceArgs {
     int* err = nullptr;  // device error word (kErr* bits) for bounded waits
     double* corr = nullptr;  // non-null: += {Sum b, Sum b^2, Sum d, Sum b d} of the
                              // correlation of the warped image with its reference
-    bool pdl = false;        // launch as a programmatic dependent launch (TMA-fed and
-                             // split kernels; only without a stop test: they read the
+    bool pdl = false;        // launch as a programmatic dependent launch (split
+                             // kernels only; only without a stop test: they read the
                              // stop flag before waiting for the kernel before)
 };
 // plain = true: the plain-load force_kernel even where a TMA-fed kernel exists
@@ -60,7 +60,7 @@ struct SmoothArgs {
     int in_type;         // storage of in (kStore*)
     int out_type;        // storage of out
     int zchunk;          // planes per block; 0 = one wave of resident blocks
-    bool pdl = false;    // as ForceArgs::pdl (packed and x/y kernels)
+    bool pdl = false;    // as ForceArgs::pdl (the x/y kernel)
 };
 // plain = true: the 32 x 8 tile kernel (smooth_kernel) for every storage type
 // instead of the packed single-precision kernels

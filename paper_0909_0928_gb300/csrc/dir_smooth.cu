@@ -127,15 +127,12 @@ __global__ void __launch_bounds__(8 * TY, 16 / TY * 8)
         mbar_arrive_expect_tx(&full[sl], (uint32_t)G::SLOT);
         tma_load_4d(base + sl * G::SLOT_STRIDE, &tmap, bx, by, pc, comp, &full[sl]);
     };
-    pdl_trigger();
     if (tid == 0) {
         for (int sl = 0; sl < S2STAGES; ++sl) mbar_init(&full[sl], 1);
         fence_mbar_init();
         fence_proxy_async();
-        pdl_wait();
         for (int st = 0; st < S2STAGES - 1 && st < nsteps; ++st) issue(st);
     }
-    pdl_wait();  // every thread: u is written below, which the kernel before reads
     __syncthreads();
 
     f32x2 ring[K][2];
@@ -385,8 +382,8 @@ static cudaError_t launch_s2(const SmoothArgs& a, int num_sms, cudaStream_t s) {
     if (zc > a.g.nz) zc = a.g.nz;
     const int chunks = (a.g.nz + zc - 1) / zc;
     const dim3 grid((a.g.nx + S2X - 1) / S2X, (a.g.ny + TY - 1) / TY, chunks * a.ncomp);
-    return launch_ex(smooth2_kernel<R, TY>, grid, dim3(8 * TY, 1, 1), G::SMEM, s, a.pdl, map, a,
-                     zc);
+    smooth2_kernel<R, TY><<<grid, dim3(8 * TY, 1, 1), G::SMEM, s>>>(map, a, zc);
+    return cudaGetLastError();
 }
 
 // tile height: 32 rows where the level is large enough that fewer, taller

@@ -58,7 +58,8 @@ def footprint_bytes(dims, levels: int, elem: int = 4, field_elem: int | None = N
 
 def _params_key(p: DirParams) -> tuple:
     return (p.levels, tuple(p.iters[: p.levels]), p.sigma, p.alpha, p.stop_mode, p.eps,
-            p.stop_window, p.field_dtype, p.use_graph, p.precision, p.fuse, p.plain_kernels)
+            p.stop_window, p.field_dtype, p.use_graph, p.precision, p.fuse, p.plain_kernels,
+            p.correlation, p.pdl)
 
 
 def request_footprint(req) -> int:
