@@ -112,6 +112,10 @@ KERNEL_SOURCES = {
     "force_zs_kernel": ["dir_force_zs.cu", "dir_split.cuh", "dir_force_gm.cuh",
                         "dir_force_kernel.cuh", "dir_force_law.cuh", "dir_stencil.cuh",
                         "dir_common.cuh"],
+    "force_zd_kernel": ["dir_force_d.cu", "dir_split_d.cuh", "dir_split.cuh",
+                        "dir_force_kernel.cuh", "dir_stencil.cuh", "dir_common.cuh"],
+    "force_st_kernel": ["dir_force_d.cu", "dir_split_d.cuh", "dir_force_kernel.cuh",
+                        "dir_force_law.cuh", "dir_stencil.cuh", "dir_common.cuh"],
 }
 
 
@@ -631,9 +635,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--form", default="plain",
                     choices=["plain", "batch", "study", "precision", "serve"])
-    ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2, 3],
-                    help="iteration schedule for Eqs. 1-2: 0 force + smoothing kernels, 1 fused, "
+    ap.add_argument("--fuse", type=int, default=2, choices=[0, 1, 2, 3, 4],
+                    help="iteration schedule: 0 force + smoothing kernels, 1 fused, "
                          "3 split Gaussian (x/y kernel, z pass inside the force kernel), "
+                         "4 as 3 with Eqs. 3-6 split after the difference image, "
                          "2 the library default (split where it applies)")
     args = ap.parse_args()
     args.variant_id = VARIANT_NAMES.index(args.variant)
@@ -815,6 +820,10 @@ def main():
                  "fused": "fused2_kernel", "smooth": "smooth2_kernel"}
     if schedule == 2:  # split Gaussian: x/y kernel, then z pass + force (same bytes per voxel)
         kernel_of.update(force="force_zs_kernel", smooth="smooth_xy_kernel")
+    if schedule == 3:  # Eqs. 3-6: x/y kernel, z + D kernel, stencil force kernel
+        kernel_of.update(force="force_zd_kernel+force_st_kernel", smooth="smooth_xy_kernel")
+        # z + D: t 12, S 4, M 4, u 12, D 4 (Eq. 6: + d 4); force: D 4, S 4, u 12, v 12 (+ d 4)
+        bytes_pv["force"] = 68 if args.variant_id != 5 else 76
     per_kernel = {}
     for k, (ms, n) in kt.items():
         if n:
@@ -854,7 +863,8 @@ def main():
         # Eqs. 1-2) for every force law, plus Eqs. 1-2 with the two-kernel
         # schedule everywhere (0) and passive fused everywhere (1)
         for vid, alpha, fuse in ((0, 0.4, 2), (0, 0.4, 0), (0, 0.4, 1), (1, 0.4, 2), (1, 0.4, 0),
-                                 (2, 0.4, 2), (3, 0.4, 2), (4, 0.4, 2), (4, 2.0, 2), (5, 0.4, 2)):
+                                 (2, 0.4, 2), (2, 0.4, 0), (3, 0.4, 2), (4, 0.4, 2), (4, 2.0, 2),
+                                 (5, 0.4, 2), (5, 0.4, 0)):
             p2 = dl.dir_params_default(levels=LEVELS, iters=ITERS, alpha=alpha, fuse=fuse)
             c2 = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, vid, p2, stream)
             ms = []

@@ -112,11 +112,18 @@ typedef struct {
                                     as their own kernel plane by plane, its z pass inside the
                                     force kernel down each thread's z column (all six laws, FP32
                                     field, float or int16 images, sigma with radius 3, any
-                                    stop_mode), every level.  2 (default): split for Eqs.
+                                    stop_mode), every level.  4: as 3, but Eqs. (3)-(6) split
+                                    once more after the difference image: a z-pass kernel
+                                    writes u and D = W - S once per voxel (Eq. 6: both warped
+                                    differences) to a scratch of 4 (Eq. 6: 5) floats per voxel
+                                    of the level, and a stencil kernel forms the force from
+                                    them, instead of interpolating W on every brick's halo.
+                                    2 (default): as 4 where it applies.  dir_register_noalloc
+                                    has no scratch for the form of 4: there 2 is split for Eqs.
                                     (1)-(2) on every level and for Eqs. (3)-(6) on levels of at
                                     most 2^21 voxels, else fused on the small levels that one
                                     block per SM covers in two-plane chunks (e.g. 64 x 64 x 25),
-                                    else 0 */
+                                    else 0, and 4 is 3 */
     int plain_kernels;           /* 0 (default): the production kernels (TMA-fed bricks and
                                     plane rings, packed smoothing, fused small levels).  1: the
                                     plain-load kernels with the same per-voxel arithmetic and
@@ -153,9 +160,11 @@ typedef struct {
     float ms_fused_finest;          /* with params.timing: summed fused-iteration time at level 0, ms */
     int n_fused_finest;             /* number of launches behind ms_fused_finest */
     int schedule_finest;            /* iteration schedule of level 0: 0 force + smoothing kernels,
-                                       1 fused iteration, 2 split Gaussian (fuse = 3); with the
-                                       split schedule ms_smooth_finest times the x/y kernel and
-                                       ms_force_finest the z + force kernel */
+                                       1 fused iteration, 2 split Gaussian (fuse = 3), 3 split
+                                       with the difference image (fuse = 4); with a split
+                                       schedule ms_smooth_finest times the x/y kernel and
+                                       ms_force_finest the z + force kernel (3: the z + D and
+                                       the stencil force kernels together) */
 } dir_stats;
 
 /* Fills *p with the defaults listed above.  Returns DIR_EINVAL if p is NULL. */

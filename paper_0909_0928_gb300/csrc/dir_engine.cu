@@ -129,6 +129,8 @@ struct dir_ctx {
     char* img_pool = nullptr;
     char* A = nullptr;
     char* B = nullptr;
+    char* C = nullptr;     // Eqs. 3-6 split with the difference image: u and D of a level
+    size_t C_bytes = 0;
     double* red = nullptr;
     double* corr = nullptr;   // 4 sums per iteration of the correlation coefficient, or null
     double* lhist = nullptr;
@@ -256,35 +258,63 @@ static bool level_pdl(const dir_ctx* c, const Grid3& g, bool timed) {
            (long long)g.nx * g.ny * g.nz > (1LL << 18);
 }
 
+// The split kernels: FP32 field, float or int16 images, radius 3
+static bool level_split_ok(const dir_ctx* c, int l) {
+    return !c->fp64 && !c->p.plain_kernels && c->field_type == dirk::kStoreF32 &&
+           (c->img_type(l) == dirk::kStoreF32 || c->img_type(l) == dirk::kStoreI16) &&
+           c->taps.R == 3;
+}
+
+// Schedule 3, Eqs. 3-6 only: the split iteration with the difference image
+// formed once per voxel (x/y kernel, z + D kernel, stencil force kernel), on
+// every level with fuse = 2 or 4.  Measured per iteration on the 256x256x100
+// pyramid against the one-pass z + force kernel (schedule 2) and, on the
+// finest level, the force + smoothing kernels (schedule 0), active: 125.4 us
+// against 169.7 and 148.6 on the finest level, 21.7 against 27.8 on
+// 128x128x50, 10.2 against 10.5 on 64x64x25; Eq. 6: 170.8 against 229.1 and
+// 207.8, 36.6 against 45.4, 16.8 against 17.8.  It needs the u + D scratch
+// (dir_ctx::C), allocated for the levels that run it; without one
+// (dir_register_noalloc) a level runs what the rules below give.
+static bool level_wants_d(const dir_ctx* c, int l) {
+    if (c->variant < 2 || !level_split_ok(c, l)) return false;
+    return c->p.fuse == 2 || c->p.fuse == 4;
+}
+
+static size_t level_d_bytes(const dir_ctx* c, int l) {
+    return (size_t)dirk::force_d_planes(c->variant) * (size_t)c->lv[l].g.cs * sizeof(float);
+}
+
 // Iteration schedule of pyramid level l: 0 force + smoothing kernels, 1 fused
 // iteration (the Gaussian of v_{k-1} folded into the force pass), 2 split
 // Gaussian (its x and y passes as their own kernel, its z pass inside the
-// force kernel).  All three give the same field bit for bit.  fuse = 2 (the
-// default) takes the split schedule where it applies (FP32 field, radius 3) for
-// Eqs. 1-2 on every level and for Eqs. 3-6 on the small levels, otherwise the
-// fused one on the small levels: measured per level on the 256x256x100 pyramid.
+// force kernel), 3 split with the difference image (above).  All four give the
+// same field bit for bit.  fuse = 2 (the default) takes the split schedule
+// where it applies for Eqs. 1-2 on every level and for Eqs. 3-6 on the small
+// levels (there in form 3), otherwise the fused one on the small levels:
+// measured per level on the 256x256x100 pyramid.
 static int level_schedule(const dir_ctx* c, int l) {
     if (c->fp64 || c->p.plain_kernels) return 0;
     const Grid3& g = c->lv[l].g;
-    const bool split_ok = c->field_type == dirk::kStoreF32 &&
-                          (c->img_type(l) == dirk::kStoreF32 || c->img_type(l) == dirk::kStoreI16) &&
-                          c->taps.R == 3;
+    const bool split_ok = level_split_ok(c, l);
+    if (level_wants_d(c, l) && c->C && c->C_bytes >= level_d_bytes(c, l)) return 3;
     const bool eqs12 = c->variant == 0 || c->variant == 1;
     const bool fused_ok = c->p.stop_mode == 0 && dirk::fused_supported(c->variant) &&
                           c->field_type == c->real_type && c->img_type(l) == c->real_type;
     switch (c->p.fuse) {
         case 1: return fused_ok ? 1 : 0;
         case 2: {
-            // Eqs. 3-6 need u on the brick's one-voxel halo too, so their split
-            // kernel runs the z pass on 34 x 10 columns of a deeper box: it pays
-            // on levels of at most 2^21 voxels (the marching smoothing's z halo
+            // (Eqs. 3-6 here only without the scratch of schedule 3.)  They
+            // need u on the brick's one-voxel halo too, so their split kernel
+            // runs the z pass on 34 x 10 columns of a deeper box: it pays on
+            // levels of at most 2^21 voxels (the marching smoothing's z halo
             // costs more there) and not above (256x256x100, active: 137 us
             // against 98 + 54 - 37 us per finest iteration)
             const bool small = (long long)g.nx * g.ny * g.nz <= (1LL << 21);
             if (split_ok && (eqs12 || small)) return 2;
             return fused_ok && dirk::fused_small_level(g, c->num_sms) ? 1 : 0;
         }
-        case 3: return split_ok ? 2 : 0;
+        case 3:
+        case 4: return split_ok ? 2 : 0;
         default: return 0;
     }
 }
@@ -479,10 +509,11 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             c->fused_level[lc] = 1;
             continue;
         }
-        if (sched == 2 && n > 0) {
+        if ((sched == 2 || sched == 3) && n > 0) {
             // iteration 0 from u; iteration k > 0: t = G_y G_x v (xy kernel), then
-            // v = u - dr(u) with u = G_z t (force kernel); then u = G v of the last
-            // iteration run
+            // v = u - dr(u) with u = G_z t (force kernel; schedule 3: the z + D
+            // kernel writes u and D to the scratch, the stencil force kernel
+            // reads them); then u = G v of the last iteration run
             char* vbuf = oth;
             char* tbuf = cur;
             dirk::SmoothArgs xa = sa;
@@ -491,8 +522,9 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             xa.zchunk = c->tune_zchunk[l];  // 0: the launcher's own chunking
             // brick depths: of the z + force kernel (tuned or its own rule), and
             // of the plain force pass of iteration 0
-            const int zs_depth =
-                c->tune_depth[l] ? c->tune_depth[l] : dirk::force_zs_depth(c->variant, g, c->num_sms);
+            const int zs_depth = c->tune_depth[l] ? c->tune_depth[l]
+                                 : sched == 3 ? dirk::force_d_depth(g, c->num_sms)
+                                              : dirk::force_zs_depth(c->variant, g, c->num_sms);
             const int first_depth = dirk::force_brick_depth(g, c->num_sms);
             const bool pdl = level_pdl(c, g, timed);
             for (int it = 0; it < n; ++it, ++row) {
@@ -513,11 +545,25 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     xa.pdl = pdl;
                     CK(c, dirk::launch_smooth_xy(xa, c->num_sms, s));
                     if (timed && record(c, e[1], s, capturing) != DIR_OK) return DIR_ECUDA;
-                    fa.u = tbuf;
                     fa.depth = zs_depth;
                     fa.pdl = pdl;
-                    CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
-                    c->launches += 2;
+                    if (sched == 3) {
+                        dirk::ForceArgs za = fa, ta = fa;
+                        char* dpl = c->C + 3 * (size_t)g.cs * sizeof(float);
+                        za.u = tbuf;
+                        za.v = c->C;
+                        za.dbuf = ta.dbuf = dpl;
+                        za.dbuf2 = ta.dbuf2 =
+                            c->variant == DIR_INVERSE_CONSISTENT ? dpl + (size_t)g.cs * sizeof(float)
+                                                                 : nullptr;
+                        ta.u = c->C;
+                        CK(c, dirk::launch_force_d(c->variant, za, ta, c->taps, s));
+                        c->launches += 3;
+                    } else {
+                        fa.u = tbuf;
+                        CK(c, dirk::launch_force_zs(c->variant, fa, c->taps, s));
+                        c->launches += 2;
+                    }
                 }
                 if (timed && record(c, e[2], s, capturing) != DIR_OK) return DIR_ECUDA;
                 if (c->p.stop_mode >= 1) {
@@ -537,7 +583,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
             c->launches += 1;
             cur = tbuf;
             oth = vbuf;
-            c->fused_level[lc] = 2;
+            c->fused_level[lc] = sched;
             continue;
         }
         c->fused_level[lc] = 0;
@@ -606,7 +652,7 @@ static void release(dir_ctx* c) {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap) cudaStreamDestroy(c->cap);
-    void* bufs[] = {c->img_pool, c->A, c->B, c->red, c->corr, c->lhist, c->ctl, c->derr,
+    void* bufs[] = {c->img_pool, c->A, c->B, c->C, c->red, c->corr, c->lhist, c->ctl, c->derr,
                     c->stage_img, c->stage_f32, c->stage_f64};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, c->stream);
@@ -628,7 +674,7 @@ static int validate_params(const dir_params* p) {
     if (p->field_dtype != DIR_F32 && p->field_dtype != DIR_BF16) return DIR_EUNSUPPORTED;
     if (p->field_dtype == DIR_BF16 && p->precision != DIR_F32) return DIR_EUNSUPPORTED;
     if (p->init_field && p->levels != 1) return DIR_EINVAL;
-    if (p->fuse < 0 || p->fuse > 3) return DIR_EINVAL;
+    if (p->fuse < 0 || p->fuse > 4) return DIR_EINVAL;
     if (p->plain_kernels != 0 && p->plain_kernels != 1) return DIR_EINVAL;
     return DIR_OK;
 }
@@ -786,6 +832,15 @@ int dir_create(dir_ctx** out, const void* static_img, const void* moving_img, co
         c->lv[l].S = c->img_pool + img_off[l][0];
         c->lv[l].M = c->img_pool + img_off[l][1];
     }
+    // the u + D scratch of schedule 3, for the largest level that runs it
+    for (int l = 0; l < c->levels; ++l)
+        if (p.iters[c->levels - 1 - l] > 0 && level_wants_d(c, l))
+            c->C_bytes = std::max(c->C_bytes, level_d_bytes(c, l));
+    if (c->C_bytes > 0 && cudaMallocAsync(&c->C, c->C_bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "device allocation failed";
+        return fail(DIR_ENOMEM);
+    }
     e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
@@ -909,7 +964,7 @@ int dir_sync(dir_ctx* c, dir_stats* st) {
         if (c->p.timing) {
             const int runs = c->iters_run[fin];
             const bool fused = c->fused_level[fin] == 1;
-            const bool split = c->fused_level[fin] == 2;
+            const bool split = c->fused_level[fin] >= 2;
             for (int i = 0; i < c->n_timed && i < runs; ++i) {
                 float a = 0.f, b = 0.f;
                 CK(c, cudaEventElapsedTime(&a, c->tev[3 * i], c->tev[3 * i + 1]));
@@ -1464,15 +1519,28 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         fa.field_type = c->field_type;
         fa.err = c->derr;
         fa.pf_stride = c->num_sms;  // as in the registration
-        const bool split = level_schedule(c, l) == 2;  // time the kernels the level runs
+        const int sched = level_schedule(c, l);  // time the kernels the level runs
+        const bool split = sched >= 2;
         float best = 1e30f;
         int best_d = 0;
         const int depths[5] = {1, 2, 4, 8, 6};  // 6: the split force kernel only
-        for (int di = 0; di < (split ? 5 : 4) && rc == DIR_OK; ++di) {
+        // schedule 3: the z + D and stencil force kernels, u and D in the scratch
+        dirk::ForceArgs za = fa, ta = fa;
+        if (sched == 3) {
+            char* dpl = c->C + 3 * (size_t)g.cs * sizeof(float);
+            za.v = c->C;
+            ta.u = c->C;
+            za.dbuf = ta.dbuf = dpl;
+            za.dbuf2 = ta.dbuf2 = c->variant == DIR_INVERSE_CONSISTENT
+                                      ? dpl + (size_t)g.cs * sizeof(float)
+                                      : nullptr;
+        }
+        for (int di = 0; di < (sched == 2 ? 5 : 4) && rc == DIR_OK; ++di) {
             const int d = depths[di];
-            fa.depth = d;
+            fa.depth = za.depth = ta.depth = d;
             float ms = 0.0f;
             rc = timed([&]() {
+                if (sched == 3) return dirk::launch_force_d(c->variant, za, ta, c->taps, c->stream);
                 if (split) return dirk::launch_force_zs(c->variant, fa, c->taps, c->stream);
                 return dirk::launch_force(c->variant, c->fp64, fa, c->stream, c->p.plain_kernels != 0);
             }, &ms);

@@ -39,6 +39,10 @@ struct ForceArgs {
     bool pdl = false;        // launch as a programmatic dependent launch (split
                              // kernels only; only without a stop test: they read the
                              // stop flag before waiting for the kernel before)
+    void* dbuf = nullptr;    // Eqs. 3-6 split with the difference image: D = W - S
+                             // (Eq. 6: D_m + D_s), one float per voxel, pitched as a
+                             // field component
+    void* dbuf2 = nullptr;   // Eq. 6 only: d = D_m - D_s, likewise
 };
 // plain = true: the plain-load force_kernel even where a TMA-fed kernel exists
 // (the same per-voxel arithmetic without the tiling; a cross-check of it)
@@ -80,6 +84,18 @@ cudaError_t launch_smooth_xy(const SmoothArgs& a, int num_sms, cudaStream_t s);
 bool force_zs_supported(int variant, const ForceArgs& a, const Taps& taps);
 int force_zs_depth(int variant, const Grid3& g, int num_sms);
 cudaError_t launch_force_zs(int variant, const ForceArgs& a, const Taps& taps, cudaStream_t s);
+
+// Eqs. 3-6, the split iteration with the difference image formed once per
+// voxel (dir_split_d.cuh): after launch_smooth_xy, the z + D pass (zd: u = t,
+// v = the u it writes, dbuf / dbuf2 = the D it writes) and the stencil force
+// pass (st: u = that u, v = the field out, dbuf / dbuf2 = that D), each with
+// its own brick depth (1, 2, 4 or 8; 6 runs as 4).  force_d_planes: floats per
+// voxel of the u + D scratch (4, Eq. 6: 5).
+bool force_d_supported(int variant, const ForceArgs& a, const Taps& taps);
+int force_d_planes(int variant);
+int force_d_depth(const Grid3& g, int num_sms);
+cudaError_t launch_force_d(int variant, const ForceArgs& zd, const ForceArgs& st, const Taps& taps,
+                           cudaStream_t s);
 
 // Grouped launches of the split schedule: one kernel over the blocks of up to
 // kGroupMax volumes (the same pyramid level of several registrations, each

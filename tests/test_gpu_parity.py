@@ -341,14 +341,21 @@ def test_state_errors(dl, small_phantom):
     assert e.value.code == dlm.DIR_EINVAL
 
 
-@pytest.mark.parametrize("fuse", [1, 0, 3])
+@pytest.mark.parametrize("fuse", [1, 0, 3, 4])
 def test_timing_stats(dl, small_phantom, fuse):
     S, M = small_phantom["S"], small_phantom["M"]
+    variant = 2 if fuse == 4 else 0
     for graph in (1, 0):
-        g = gpu_register(dl, S, M, 0, 2, [4, 7], timing=1, use_graph=graph, fuse=fuse)
+        g = gpu_register(dl, S, M, variant, 2, [4, 7], timing=1, use_graph=graph, fuse=fuse)
         st = g["stats"]
-        assert st["schedule_finest"] == {0: 0, 1: 1, 3: 2}[fuse]
-        if fuse == 3:
+        assert st["schedule_finest"] == {0: 0, 1: 1, 3: 2, 4: 3}[fuse]
+        if fuse == 4:
+            # per level: plain force, then x/y + z/D + stencil kernels, one
+            # smoothing; the x/y launches and the z/D + stencil pairs of
+            # iterations > 0 are timed
+            assert st["n_force_finest"] == 6 and st["n_smooth_finest"] == 6
+            assert st["kernel_launches"] == 2 * 2 + 1 + 2 + 3 * 3 + 2 + 3 * 6
+        elif fuse == 3:
             # per level: plain force, then x/y + z/force kernels, one smoothing;
             # the x/y and z/force launches of iterations > 0 are timed
             assert st["n_force_finest"] == 6 and st["n_smooth_finest"] == 6
@@ -564,10 +571,17 @@ def test_split_schedule_matches_plain_kernels_full_size(dl, full_phantom, varian
 
 
 @pytest.mark.parametrize("variant", [2, 3, 4, 5])
+def test_difference_image_split_matches_plain_kernels_full_size(dl, full_phantom, variant):
+    # fuse = 4: Eqs. 3-6 as x/y kernel, z + D kernel (u and D = W - S once per
+    # voxel) and stencil force kernel on every level, the finest included
+    S, M = full_phantom["S"], full_phantom["M"]
+    _tight(dl, S, M, variant, 0.4, 3, [20, 10, 5], 4, f"3x20/10/5 split-D v{variant}")
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 def test_default_schedule_matches_plain_kernels_full_size(dl, full_phantom, variant):
-    # the default for Eqs. 3-6: split on the two coarse levels, force +
-    # smoothing kernels on the finest; the field crosses between schedules at
-    # each upsampling
+    # the default for Eqs. 3-6: split with the difference image on every
+    # level (as fuse = 4), the scratch sized for the finest
     S, M = full_phantom["S"], full_phantom["M"]
     _tight(dl, S, M, variant, 0.4, 3, [20, 10, 5], 2, f"3x20/10/5 default v{variant}")
 
@@ -587,15 +601,18 @@ def test_split_schedule_ragged(dl, dims):
         S, M = make_blob_pair(dims, (0.6, -0.4, 0.3), seed=5, n_blobs=8, sigma_vox=2.0, noise=0.3)
     for variant in (0, 1, 3, 5):
         _tight(dl, S, M, variant, 0.4, 3, [12, 8, 6], 3, f"{dims} split v{variant}")
+    for variant in (2, 5):
+        _tight(dl, S, M, variant, 0.4, 3, [12, 8, 6], 4, f"{dims} split-D v{variant}")
 
 
-def test_split_schedule_with_stop_test(dl, small_phantom):
+@pytest.mark.parametrize("variant,fuse", [(0, 3), (3, 4)])
+def test_split_schedule_with_stop_test(dl, small_phantom, variant, fuse):
     # the stop test ends a level early: the split kernels skip the rest and
     # the last smoothing still runs on the last v
     S, M = small_phantom["S"], small_phantom["M"]
     kw = dict(stop_mode=1, eps=2e-3, window=10)
-    a = gpu_register(dl, S, M, 0, 2, [300, 300], fuse=3, **kw)
-    b = gpu_register(dl, S, M, 0, 2, [300, 300], plain=1, **kw)
+    a = gpu_register(dl, S, M, variant, 2, [300, 300], fuse=fuse, **kw)
+    b = gpu_register(dl, S, M, variant, 2, [300, 300], plain=1, **kw)
     runs = a["stats"]["iters_run"][:2]
     assert runs == b["stats"]["iters_run"][:2] and min(runs) < 300, runs
     assert np.array_equal(a["u"], b["u"])
@@ -606,28 +623,35 @@ def test_split_schedule_int16_images(dl, full_phantom):
     S = np.round(full_phantom["S"]).astype(np.int16)
     M = np.round(full_phantom["M"]).astype(np.int16)
     nz, ny, nx = S.shape
-    out = {}
-    for fuse, dt, (Si, Mi) in ((3, dl.DIR_I16, (S, M)),
-                               (0, dl.DIR_F32, (S.astype(np.float32), M.astype(np.float32)))):
-        params = dl.dir_params_default(levels=3, iters=[20, 10, 5], fuse=fuse)
-        ctx = dl.dir_create(torch.from_numpy(Si).cuda(), torch.from_numpy(Mi).cuda(),
-                            (nx, ny, nz), FULL_SPACING, dt, True, 0, params,
-                            torch.cuda.current_stream())
-        try:
-            st = dl.dir_register(ctx)
-            u = np.empty((3, nz, ny, nx), np.float32)
-            dl.dir_get_field(ctx, u)
-        finally:
-            dl.dir_destroy(ctx)
-        out[fuse] = (u, st.schedule_finest)
-    assert out[3][1] == 2 and out[0][1] == 0
-    assert np.array_equal(out[3][0], out[0][0])
+    for variant, fuse_split, sched in ((0, 3, 2), (5, 4, 3)):
+        out = {}
+        for fuse, dt, (Si, Mi) in ((fuse_split, dl.DIR_I16, (S, M)),
+                                   (0, dl.DIR_F32, (S.astype(np.float32), M.astype(np.float32)))):
+            params = dl.dir_params_default(levels=3, iters=[20, 10, 5], fuse=fuse)
+            ctx = dl.dir_create(torch.from_numpy(Si).cuda(), torch.from_numpy(Mi).cuda(),
+                                (nx, ny, nz), FULL_SPACING, dt, True, variant, params,
+                                torch.cuda.current_stream())
+            try:
+                st = dl.dir_register(ctx)
+                u = np.empty((3, nz, ny, nx), np.float32)
+                dl.dir_get_field(ctx, u)
+            finally:
+                dl.dir_destroy(ctx)
+            out[fuse] = (u, st.schedule_finest)
+        assert out[fuse_split][1] == sched and out[0][1] == 0
+        assert np.array_equal(out[fuse_split][0], out[0][0]), f"v{variant} fuse {fuse_split}"
 
 
 @pytest.mark.parametrize("variant", [0, 1, 3, 5])
 def test_split_schedule_matches_plain_kernels_max_size(dl, wave_max, variant):
     S, M = wave_max
     _tight(dl, S, M, variant, 0.4, 1, [5], 3, f"512x512x160 split v{variant}")
+
+
+@pytest.mark.parametrize("variant", [2, 5])
+def test_difference_image_split_matches_plain_kernels_max_size(dl, wave_max, variant):
+    S, M = wave_max
+    _tight(dl, S, M, variant, 0.4, 1, [5], 4, f"512x512x160 split-D v{variant}")
 
 
 # ------------------------------------------------------------ maximum size
