@@ -1234,10 +1234,18 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
             const int rc = enqueue_level_start(c, lc, cur[q], oth[q], s);
             if (rc != DIR_OK) return rc;
             c->level_first[lc] = row[q];
-            c->fused_level[lc] = iters > 0 ? 2 : 0;
+            c->fused_level[lc] = 0;
             grids[q] = c->lv[l].g;
         }
         if (iters == 0) continue;
+        // Eqs. 3-6 where every job has its u + D scratch: the split after the
+        // difference image, as each job's own registration would run it
+        bool dform = c0->variant >= 2;
+        for (int q = 0; q < n; ++q) {
+            const dir_ctx* c = ctxs[jobs[q]];
+            dform = dform && c->C && c->C_bytes >= level_d_bytes(c, l);
+        }
+        for (int q = 0; q < n; ++q) ctxs[jobs[q]]->fused_level[lc] = dform ? 3 : 2;
         // iteration 0 from the level's starting field, per job
         for (int q = 0; q < n; ++q) {
             dir_ctx* c = ctxs[jobs[q]];
@@ -1255,11 +1263,13 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
         dirk::group_shapes(c0->variant, grids.data(), n, c0->num_sms, &ty, &zc, &depth);
         dirk::XYGroup X;
         dirk::ZSGroup Z;
+        dirk::ZDGroup ZD;
+        dirk::STGroup ST;
         X.ty = ty;
         X.zchunk = zc;
-        Z.variant = c0->variant;
-        Z.depth = depth;
-        Z.taps = c0->taps;
+        Z.variant = ZD.variant = ST.variant = c0->variant;
+        Z.depth = ZD.depth = ST.depth = depth;
+        Z.taps = ZD.taps = c0->taps;
         for (int q = 0; q < n; ++q) {
             dir_ctx* c = ctxs[jobs[q]];
             dirk::SmoothArgs sa = level_smooth_args(c, lc);
@@ -1272,7 +1282,21 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
             fa.v = oth[q];
             fa.stop_iter = nullptr;
             fa.depth = depth;
-            if (!dirk::xy_group_add(X, sa) || !dirk::zs_group_add(Z, fa)) {
+            bool added = dirk::xy_group_add(X, sa);
+            if (dform) {
+                dirk::ForceArgs za = fa, ta = fa;
+                char* dpl = c->C + 3 * (size_t)grids[q].cs * sizeof(float);
+                za.v = c->C;
+                ta.u = c->C;
+                za.dbuf = ta.dbuf = dpl;
+                za.dbuf2 = ta.dbuf2 = c->variant == DIR_INVERSE_CONSISTENT
+                                          ? dpl + (size_t)grids[q].cs * sizeof(float)
+                                          : nullptr;
+                added = added && dirk::d_group_add(ZD, ST, za, ta);
+            } else {
+                added = added && dirk::zs_group_add(Z, fa);
+            }
+            if (!added) {
                 c->err = "grouped batch: a tensor map could not be made";
                 return DIR_EINVAL;
             }
@@ -1285,14 +1309,19 @@ static int enqueue_grouped_chunk(dir_ctx* const* ctxs, const std::vector<int>& j
             for (int q = 0; q < n; ++q) {
                 dir_ctx* c = ctxs[jobs[q]];
                 const size_t r = (size_t)(row[q] + it);
-                Z.a[q].red = c->red + 3 * r;
-                Z.a[q].corr = c->corr ? c->corr + 4 * r : nullptr;
-                Z.a[q].iter = it;
+                dirk::ForceArgs& fa = dform ? ST.a[q] : Z.a[q];
+                fa.red = c->red + 3 * r;
+                fa.corr = c->corr ? c->corr + 4 * r : nullptr;
+                fa.iter = it;
+                ZD.a[q].iter = it;
                 X.a[q].iter = it;
-                c->launches += 2;
+                c->launches += dform ? 3 : 2;
             }
             CK(c0, dirk::launch_smooth_xy_grouped(X, s, pdl));
-            CK(c0, dirk::launch_force_zs_grouped(c0->variant, img, Z, s, pdl));
+            if (dform)
+                CK(c0, dirk::launch_force_d_grouped(img, ZD, ST, s, pdl));
+            else
+                CK(c0, dirk::launch_force_zs_grouped(c0->variant, img, Z, s, pdl));
         }
         // u = G v of the last iteration, per job
         for (int q = 0; q < n; ++q) {

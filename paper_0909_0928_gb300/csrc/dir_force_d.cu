@@ -122,12 +122,16 @@ bool force_d_supported(int variant, const ForceArgs& a, const Taps& taps) {
 
 int force_d_planes(int variant) { return variant == 5 ? 5 : 4; }
 
-// 4-deep bricks for both kernels on every level: the autotuner's choice, or
-// within 1 % of it, on the three levels of the 256x256x100 pyramid
+// Brick depth of both kernels: 8 where such bricks still number four per SM,
+// else the deepest of 4 and 2 that gives one per SM, else 1 -- 8, 4 and 2 on
+// the 256x256x100 pyramid, the autotuner's choice there for Eq. 3 and Eq. 6
+// (Eq. 3: 10.46 ms per registration against 10.63 with 4 on every level)
 int force_d_depth(const Grid3& g, int num_sms) {
-    (void)g;
-    (void)num_sms;
-    return 4;
+    const long long bxy = (long long)((g.nx + FTX - 1) / FTX) * ((g.ny + FTY - 1) / FTY);
+    if (bxy * ((g.nz + 7) / 8) >= 4LL * num_sms) return 8;
+    for (int d = 4; d >= 2; d /= 2)
+        if (bxy * ((g.nz + d - 1) / d) >= num_sms) return d;
+    return 1;
 }
 
 cudaError_t launch_force_d(int variant, const ForceArgs& zd, const ForceArgs& st, const Taps& taps,

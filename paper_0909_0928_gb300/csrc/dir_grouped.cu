@@ -12,10 +12,12 @@
 
 #include "dir_launch.h"
 #include "dir_split.cuh"
+#include "dir_split_d.cuh"
 
 namespace dirk {
 
-static_assert(sizeof(XYGroup) < 30000 && sizeof(ZSGroup) < 30000,
+static_assert(sizeof(XYGroup) < 30000 && sizeof(ZSGroup) < 30000 && sizeof(ZDGroup) < 30000 &&
+                  sizeof(STGroup) < 30000,
               "grouped launch parameters must fit the kernel parameter space");
 
 __device__ __forceinline__ int group_job(const int* first, int n, int b) {
@@ -47,6 +49,22 @@ __global__ void __launch_bounds__(FNT, (V >= 2 && FTZ >= 2) ? 3 : 4)
         zs_block<V, FTZ, TI>(&G.tmap[j], &G.smap[j], &G.mmap[j], G.a[j], G.taps, bp);
     else
         gzs_block<V, FTZ, TI>(&G.tmap[j], &G.smap[j], &G.mmap[j], G.a[j], G.taps, bp);
+}
+
+template <int V, int FTZ, typename TI>
+__global__ void __launch_bounds__(FNT, 4) force_zd_grouped_kernel(const __grid_constant__ ZDGroup G) {
+    const int b = blockIdx.x;
+    const int j = group_job(G.first, G.n, b);
+    zd_block<V, FTZ, TI>(&G.tmap[j], G.a[j], G.taps,
+                         group_pos(b - G.first[j], G.gx[j], G.gy[j], G.gz[j]));
+}
+
+template <int V, int FTZ, typename TI>
+__global__ void __launch_bounds__(FNT, 4) force_st_grouped_kernel(const __grid_constant__ STGroup G) {
+    const int b = blockIdx.x;
+    const int j = group_job(G.first, G.n, b);
+    st_block<V, FTZ, TI>(&G.dmap[j], &G.smap[j], &G.umap[j], &G.emap[j], G.a[j],
+                         group_pos(b - G.first[j], G.gx[j], G.gy[j], G.gz[j]));
 }
 
 // x/y kernel shared memory of a tile height
@@ -230,6 +248,91 @@ cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G,
     if (G.n < 1 || G.first[G.n] < 1 || variant != G.variant) return cudaErrorInvalidValue;
     if (img_type == kStoreF32) return launch_zsg_types<float>(variant, G, s, pdl);
     if (img_type == kStoreI16) return launch_zsg_types<int16_t>(variant, G, s, pdl);
+    return cudaErrorInvalidValue;
+}
+
+bool d_group_add(ZDGroup& Z, STGroup& T, const ForceArgs& zd, const ForceArgs& st) {
+    const int d = Z.depth;
+    if (Z.n >= kGroupMax || Z.n != T.n || T.depth != d || Z.variant < 2 || Z.variant > 5 ||
+        T.variant != Z.variant || zd.field_type != kStoreF32 ||
+        (zd.img_type != kStoreF32 && zd.img_type != kStoreI16) || Z.taps.R != FZR ||
+        !(d == 1 || d == 2 || d == 4) || zd.dbuf == nullptr || st.dbuf == nullptr ||
+        (Z.variant == 5 && (zd.dbuf2 == nullptr || st.dbuf2 == nullptr)))
+        return false;
+    const int j = Z.n;
+    if (j == 0) Z.first[0] = T.first[0] = 0;
+    const bool i16 = zd.img_type == kStoreI16;
+    const int esz = i16 ? 2 : 4;
+    const int fsw = FTX + 2 * (16 / esz);  // S box: 16 bytes of x halo each side
+    const CUtensorMapDataType it = i16 ? tma_type<int16_t>() : tma_type<float>();
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint32_t tbox[4] = {(cuuint32_t)FTX, (cuuint32_t)FTY, (cuuint32_t)(d + 2 * FZR), 3u};
+    const cuuint32_t dbox[4] = {(cuuint32_t)(FTX + 8), (cuuint32_t)(FTY + 2), (cuuint32_t)(d + 2), 1u};
+    const cuuint32_t sbox[4] = {(cuuint32_t)fsw, (cuuint32_t)(FTY + 2), (cuuint32_t)(d + 2), 1u};
+    const cuuint32_t ubox[4] = {(cuuint32_t)FTX, (cuuint32_t)FTY, (cuuint32_t)d, 3u};
+    const cuuint32_t ebox[4] = {(cuuint32_t)FTX, (cuuint32_t)FTY, (cuuint32_t)d, 1u};
+    if (!encode4(&Z.tmap[j], f32, zd.u, zd.g, 3, 4, tbox) ||
+        !encode4(&T.dmap[j], f32, st.dbuf, st.g, 1, 4, dbox) ||
+        !encode4(&T.smap[j], it, st.S, st.g, 1, esz, sbox) ||
+        !encode4(&T.umap[j], f32, st.u, st.g, 3, 4, ubox))
+        return false;
+    if (Z.variant == 5) {
+        if (!encode4(&T.emap[j], f32, st.dbuf2, st.g, 1, 4, ebox)) return false;
+    } else {
+        T.emap[j] = T.umap[j];  // not read
+    }
+    Z.a[j] = zd;
+    T.a[j] = st;
+    Z.gx[j] = T.gx[j] = (zd.g.nx + FTX - 1) / FTX;
+    Z.gy[j] = T.gy[j] = (zd.g.ny + FTY - 1) / FTY;
+    Z.gz[j] = T.gz[j] = (zd.g.nz + d - 1) / d;
+    Z.first[j + 1] = T.first[j + 1] = Z.first[j] + Z.gx[j] * Z.gy[j] * Z.gz[j];
+    Z.n = T.n = j + 1;
+    return true;
+}
+
+template <int V, int FTZ, typename TI>
+static cudaError_t launch_dg(const ZDGroup& Z, const STGroup& T, cudaStream_t s, bool pdl) {
+    constexpr int ZS = ZDGeom<FTZ>::SMEM, TS = STGeom<FTZ, V, TI>::SMEM;
+    static KernelSetup zst, tst;  // per instantiation
+    cudaError_t e = setup_kernel(zst, force_zd_grouped_kernel<V, FTZ, TI>, ZS);
+    if (e == cudaSuccess) e = setup_kernel(tst, force_st_grouped_kernel<V, FTZ, TI>, TS);
+    if (e != cudaSuccess) return e;
+    e = launch_ex(force_zd_grouped_kernel<V, FTZ, TI>, dim3((unsigned)Z.first[Z.n]),
+                  dim3(FTX, FTY, 1), ZS, s, pdl, Z);
+    if (e != cudaSuccess) return e;
+    return launch_ex(force_st_grouped_kernel<V, FTZ, TI>, dim3((unsigned)T.first[T.n]),
+                     dim3(FTX, FTY, 1), TS, s, pdl, T);
+}
+
+template <int V, typename TI>
+static cudaError_t launch_dg_depth(const ZDGroup& Z, const STGroup& T, cudaStream_t s, bool pdl) {
+    switch (Z.depth) {
+        case 4: return launch_dg<V, 4, TI>(Z, T, s, pdl);
+        case 2: return launch_dg<V, 2, TI>(Z, T, s, pdl);
+        case 1: return launch_dg<V, 1, TI>(Z, T, s, pdl);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TI>
+static cudaError_t launch_dg_types(const ZDGroup& Z, const STGroup& T, cudaStream_t s, bool pdl) {
+    switch (Z.variant) {
+        case 2: return launch_dg_depth<2, TI>(Z, T, s, pdl);
+        case 3: return launch_dg_depth<3, TI>(Z, T, s, pdl);
+        case 4: return launch_dg_depth<4, TI>(Z, T, s, pdl);
+        case 5: return launch_dg_depth<5, TI>(Z, T, s, pdl);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_force_d_grouped(int img_type, const ZDGroup& Z, const STGroup& T,
+                                   cudaStream_t s, bool pdl) {
+    if (Z.n < 1 || Z.n != T.n || Z.first[Z.n] < 1 || Z.variant != T.variant ||
+        Z.depth != T.depth)
+        return cudaErrorInvalidValue;
+    if (img_type == kStoreF32) return launch_dg_types<float>(Z, T, s, pdl);
+    if (img_type == kStoreI16) return launch_dg_types<int16_t>(Z, T, s, pdl);
     return cudaErrorInvalidValue;
 }
 

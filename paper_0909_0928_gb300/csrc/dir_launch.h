@@ -140,6 +140,34 @@ cudaError_t launch_smooth_xy_grouped(const XYGroup& G, cudaStream_t s, bool pdl 
 cudaError_t launch_force_zs_grouped(int variant, int img_type, const ZSGroup& G, cudaStream_t s,
                                     bool pdl = false);
 
+// The Eqs. 3-6 split after the difference image, grouped the same way: the z +
+// D kernel (each job's t map and arguments as for launch_force_d's zd) and the
+// stencil force kernel (its D, S, u and Eq. 6 d maps and arguments as for
+// st); both groups share first / gx / gy / gz and the brick depth (1, 2 or 4).
+struct ZDGroup {
+    CUtensorMap tmap[kGroupMax];
+    ForceArgs a[kGroupMax];
+    int first[kGroupMax + 1];
+    int gx[kGroupMax], gy[kGroupMax], gz[kGroupMax];
+    Taps taps;
+    int n = 0;
+    int variant = 0;
+    int depth = 0;
+};
+struct STGroup {
+    CUtensorMap dmap[kGroupMax], smap[kGroupMax], umap[kGroupMax], emap[kGroupMax];
+    ForceArgs a[kGroupMax];
+    int first[kGroupMax + 1];
+    int gx[kGroupMax], gy[kGroupMax], gz[kGroupMax];
+    int n = 0;
+    int variant = 0;
+    int depth = 0;
+};
+// Add one job to both groups (variant and depth already set on them)
+bool d_group_add(ZDGroup& Z, STGroup& T, const ForceArgs& zd, const ForceArgs& st);
+cudaError_t launch_force_d_grouped(int img_type, const ZDGroup& Z, const STGroup& T,
+                                   cudaStream_t s, bool pdl = false);
+
 // One fused iteration (Eqs. 1-2 only): u = G_sigma * vin on the fly, then the
 // force kernel's work, v = u - dr(u); red as for ForceArgs.
 struct FusedArgs {

@@ -36,10 +36,13 @@ from . import (DIR_BF16, DIR_F32, DIR_F64, DIR_I16, DirParams, dir_create, dir_d
                dir_get_field, dir_load, dir_params_default, dir_register_async, dir_sync)
 
 
-def footprint_bytes(dims, levels: int, elem: int = 4, field_elem: int | None = None) -> int:
+def footprint_bytes(dims, levels: int, elem: int = 4, field_elem: int | None = None,
+                    scratch_planes: int = 0) -> int:
     """Device bytes one context holds: pyramid images (2 per level, pitched
-    rows), two fields of the finest size, the staging buffer of the host field
-    read-back (3 N floats), plus a margin for reduction rows and padding."""
+    rows), two fields of the finest size, scratch_planes more finest-size
+    float volumes (the u + D scratch of Eqs. 3-6), the staging buffer of the
+    host field read-back (3 N floats), plus a margin for reduction rows and
+    padding."""
     nx, ny, nz = dims
     fe = elem if field_elem is None else field_elem
     total = 0
@@ -51,7 +54,7 @@ def footprint_bytes(dims, levels: int, elem: int = 4, field_elem: int | None = N
             n0 = n
         total += 2 * n * elem
         nx, ny, nz = (nx + 1) // 2, (ny + 1) // 2, (nz + 1) // 2
-    total += 6 * n0 * fe
+    total += 6 * n0 * fe + scratch_planes * n0 * 4
     stage = 3 * dims[0] * dims[1] * dims[2] * 4
     return int((total + stage) * 1.05) + (4 << 20)
 
@@ -66,7 +69,14 @@ def request_footprint(req) -> int:
     p = req.params
     elem = 8 if p.precision == DIR_F64 else 4
     fe = 2 if p.field_dtype == DIR_BF16 else elem
-    return footprint_bytes(req.dims, p.levels, elem, fe)
+    # Eqs. 3-6 under the default schedule (and fuse = 4): u and D = W - S of
+    # the finest level (Eq. 6: both warped differences); counted whenever the
+    # schedule may take it
+    planes = 0
+    if (req.variant >= 2 and p.precision != DIR_F64 and p.field_dtype != DIR_BF16
+            and p.fuse in (2, 4) and not p.plain_kernels):
+        planes = 5 if req.variant == 5 else 4
+    return footprint_bytes(req.dims, p.levels, elem, fe, planes)
 
 
 @dataclass
