@@ -280,6 +280,12 @@ static bool level_wants_d(const dir_ctx* c, int l) {
     return c->p.fuse == 2 || c->p.fuse == 4;
 }
 
+// The z + D kernel runs at most 4 deep: at 8 its 64 registers and 43 KB of
+// shared memory leave four blocks per SM and its gathers' latency shows (ncu,
+// 256x256x100, Eq. 3: 53.9 us against 50.9 us at 4), while the stencil force
+// kernel gains from 8 (38.3 us against 42.3 us)
+constexpr int kZdMaxDepth = 4;
+
 static size_t level_d_bytes(const dir_ctx* c, int l) {
     return (size_t)dirk::force_d_planes(c->variant) * (size_t)c->lv[l].g.cs * sizeof(float);
 }
@@ -550,6 +556,7 @@ static int enqueue_registration(dir_ctx* c, cudaStream_t s, bool capturing) {
                     if (sched == 3) {
                         dirk::ForceArgs za = fa, ta = fa;
                         char* dpl = c->C + 3 * (size_t)g.cs * sizeof(float);
+                        za.depth = std::min(zs_depth, kZdMaxDepth);
                         za.u = tbuf;
                         za.v = c->C;
                         za.dbuf = ta.dbuf = dpl;
@@ -1566,7 +1573,8 @@ extern "C" int dir_autotune(dir_ctx* c, int reps, int* shapes_out) {
         }
         for (int di = 0; di < (sched == 2 ? 5 : 4) && rc == DIR_OK; ++di) {
             const int d = depths[di];
-            fa.depth = za.depth = ta.depth = d;
+            fa.depth = ta.depth = d;
+            za.depth = std::min(d, kZdMaxDepth);
             float ms = 0.0f;
             rc = timed([&]() {
                 if (sched == 3) return dirk::launch_force_d(c->variant, za, ta, c->taps, c->stream);
