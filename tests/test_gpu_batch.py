@@ -101,8 +101,11 @@ def test_batch_equals_plain_registrations(dl):
             dl.dir_destroy(c)
 
 
-def test_grouped_batch_over_many_pairs_and_its_fallback(dl):
-    # 18 pairs of one force law: two launches of at most 16 jobs per step.
+@pytest.mark.parametrize("variant", [0, 2])
+def test_grouped_batch_over_many_pairs_and_its_fallback(dl, variant):
+    # 18 pairs of one force law: two launches of at most 16 jobs per step
+    # (Eq. 3: of the z + D and stencil force kernels, each job writing u and D
+    # to its own context's scratch).
     # The fields agree with plain registrations bit for bit; the histories to
     # single-precision rounding, because a grouped launch picks one brick
     # depth for the whole group and so partitions the FP32 per-block partial
@@ -112,14 +115,14 @@ def test_grouped_batch_over_many_pairs_and_its_fallback(dl):
     pairs = [_pair(100 + k, d, "f32") for k, d in enumerate(dims)]
     plain, hist = [], []
     for S, M in pairs:
-        ctx = _ctx(dl, S, M, 0, iters=(6, 4, 3))
+        ctx = _ctx(dl, S, M, variant, iters=(6, 4, 3))
         try:
             dl.dir_register(ctx)
             plain.append(_field(dl, ctx, S.shape))
             hist.append(dl.dir_get_history(ctx, 13))
         finally:
             dl.dir_destroy(ctx)
-    ctxs = [_ctx(dl, S, M, 0, iters=(6, 4, 3)) for S, M in pairs]
+    ctxs = [_ctx(dl, S, M, variant, iters=(6, 4, 3)) for S, M in pairs]
     batch = None
     try:
         batch = dl.dir_batch_create(ctxs, stream=torch.cuda.current_stream())
@@ -135,7 +138,8 @@ def test_grouped_batch_over_many_pairs_and_its_fallback(dl):
         nz, ny, nx = S.shape
         p = dl.dir_params_default(levels=3, iters=[6, 4, 3], stop_mode=1)
         odd = dl.dir_create(torch.from_numpy(S).cuda(), torch.from_numpy(M).cuda(), (nx, ny, nz),
-                            (1.0, 1.0, 2.0), dl.DIR_F32, True, 0, p, torch.cuda.current_stream())
+                            (1.0, 1.0, 2.0), dl.DIR_F32, True, variant, p,
+                            torch.cuda.current_stream())
         try:
             batch = dl.dir_batch_create(ctxs[:3] + [odd], stream=torch.cuda.current_stream())
             assert not dl.dir_batch_grouped(batch)
