@@ -14,9 +14,11 @@
 //              the reductions: a stencil with no gathers
 // The arithmetic is that of gm_force_body voxel by voxel (D by interp_rel with
 // the same operands, the same clamped neighbours, the same force call), so the
-// field is bit for bit the one of the other schedules.  Used on the small
-// pyramid levels, where one-pass blocks are bound by the latency of their
-// footprint gathers rather than by memory.
+// field is bit for bit the one of the other schedules.  The default for Eqs.
+// 3-6 on every pyramid level: the one-pass blocks were bound by issue and by
+// the latency of their footprint gathers, not by memory, so the 36 B per voxel
+// of u and D written here and read back by the force pass cost less than the
+// gathers and instructions they remove.
 #pragma once
 
 #include <cuda.h>
