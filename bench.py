@@ -737,9 +737,11 @@ def main():
     # the finest-level iteration without event records in the graph: the same
     # registration iterating only the finest level, less the one iterating
     # nowhere (pyramid, upsampling and the last smoothing are in both)
-    def untimed_ms(iters, reps=8):
-        p = dl.dir_params_default(levels=LEVELS, iters=iters, alpha=args.alpha, fuse=args.fuse)
-        c = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True, args.variant_id, p, stream)
+    def untimed_ms(iters, reps=8, variant=None, fuse=None):
+        p = dl.dir_params_default(levels=LEVELS, iters=iters, alpha=args.alpha,
+                                  fuse=args.fuse if fuse is None else fuse)
+        c = dl.dir_create(S_d, M_d, DIMS, SPACING, dl.DIR_F32, True,
+                          args.variant_id if variant is None else variant, p, stream)
         ms = []
         for i in range(reps + 3):
             flush.zero_()
@@ -878,6 +880,21 @@ def main():
                 {2: "", 0: "_two_kernel", 1: "_fused_all_levels", 3: "_split_gaussian"}[fuse]
             med = statistics.median(ms)
             per_variant[name] = {"ms_p50": med, "voxel_updates_per_s": vu_step / (med / 1e3)}
+        # the finest-level iteration of Eqs. 3 and 6 in the default schedule
+        # (x/y kernel, z + D kernel, stencil force kernel), untimed as above.
+        # Algorithmic bytes per voxel: x/y 24, z + D 36 (t 12, S 4, M 4, u 12,
+        # D 4; Eq. 6 + d 4), force 32 (D 4, S 4, u 12, v 12; Eq. 6 + d 4)
+        try:
+            for vid, bpv in ((2, 92), (5, 100)):
+                it_ms = (untimed_ms(fine_only, variant=vid, fuse=2) -
+                         untimed_ms([0] * LEVELS, variant=vid, fuse=2)) / ITERS[-1]
+                gbs = n0 * bpv / (it_ms / 1e3) / 1e9
+                per_variant[VARIANT_NAMES[vid] + "_finest_iteration"] = {
+                    "avg_ms": it_ms, "bytes_per_voxel": bpv, "achieved_gbs": gbs,
+                    "frac": gbs / peak, "method": "as roofline.finest_level_kernels."
+                                                  "iteration_untimed, default schedule"}
+        except Exception as e:  # reported, never fatal to the bench line
+            per_variant["eqs3_6_finest_iteration_error"] = repr(e)
 
     dl.dir_destroy(ctx)
     cpu = None
